@@ -1,0 +1,429 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself.
+
+Every check here is independent of ``oracle/``'s own formulas: dense Kronecker
+solves of Eq. (2.1), closed forms, textbook library routines, invariants of the
+Lyapunov equation, and the paper's printed iteration counts (Table 4.1).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import lyapgen as gen
+import oracle as O
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def kron_solve(A, W):
+    """(I (x) A + A (x) I) vec X = -vec W, Eq. (2.1), solved densely."""
+    n = A.shape[0]
+    I = np.eye(n)
+    M = np.kron(I, A) + np.kron(A, I)
+    x = np.linalg.solve(M, -W.reshape(-1, order="F"))
+    return x.reshape(n, n, order="F")
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+# ----------------------------------------------------------------- exact solver
+
+@pytest.mark.parametrize("n", [1, 2, 5, 17, 30])
+def test_bartels_stewart_vs_kronecker(n):
+    g = gen.rng(100 + n)
+    d = gen.random_stable(n, 3, g)
+    A, L = d["A"], d["L"]
+    W = L @ L.T
+    X = O.bartels_stewart(A, W)
+    assert rel(X, kron_solve(A, W)) < 1e-12
+
+
+def test_bartels_stewart_indefinite_rhs_vs_kronecker():
+    g = gen.rng(7)
+    A = gen.random_stable(20, 2, g)["A"]
+    B = g.standard_normal((20, 20))
+    W = B + B.T
+    assert rel(O.bartels_stewart(A, W), kron_solve(A, W)) < 1e-12
+
+
+def test_bartels_stewart_diagonal_closed_form():
+    g = gen.rng(3)
+    a = -10.0 ** g.uniform(-2, 2, 40)
+    L = g.standard_normal((40, 3))
+    W = L @ L.T
+    X = O.bartels_stewart(np.diag(a), W)
+    Xc = -W / (a[:, None] + a[None, :])
+    assert rel(X, Xc) < 1e-13
+
+
+def test_bartels_stewart_sine_basis_closed_form():
+    # A = -V diag(d) V^T with V the symmetric orthogonal sine matrix (Sec. 4.2 generator):
+    # V^T X V has entries (V^T W V)_ij / (d_i + d_j).
+    d = gen.paper_synthetic(60, 2.0)
+    V, dd, A, L = d["V"], d["d"], d["A"], d["L"]
+    assert np.linalg.norm(V @ V - np.eye(60)) < 1e-12
+    W = L @ L.T
+    Wt = V @ W @ V
+    X = V @ (Wt / (dd[:, None] + dd[None, :])) @ V
+    assert rel(O.bartels_stewart(A, W), X) < 1e-12
+
+
+def schur_blocks_solution(Q, alpha, beta, W):
+    """Closed form for A = Q T Q^T with T = blkdiag([[-a, b], [-b, -a]]) (block-diagonal Schur form)."""
+    n = Q.shape[0]
+    nb = n // 2
+    Wt = Q.T @ W @ Q
+    T = np.zeros((nb, 2, 2))
+    T[:, 0, 0] = T[:, 1, 1] = -alpha
+    T[:, 0, 1] = beta
+    T[:, 1, 0] = -beta
+    I2 = np.eye(2)
+    # block (i, j): T_i Y + Y T_j^T = -Wt_ij  <=>  (I (x) T_i + T_j (x) I) vec Y = -vec Wt_ij
+    M = np.einsum("ab,icd->iacbd", I2, T).reshape(nb, 1, 4, 4) + \
+        np.einsum("jab,cd->jacbd", T, I2).reshape(1, nb, 4, 4)
+    Wb = Wt.reshape(nb, 2, nb, 2).transpose(0, 2, 3, 1).reshape(nb, nb, 4)  # vec (column-major)
+    Y = np.linalg.solve(M, -Wb[..., None])[..., 0]
+    Xt = Y.reshape(nb, nb, 2, 2).transpose(0, 3, 1, 2).reshape(n, n)
+    return Q @ Xt @ Q.T
+
+
+def test_schur_block_closed_form_is_kronecker():
+    d = gen.normal_blocks(n=12, p=2, m=3)
+    A, L, S = d["A"], d["L"], d["S"]
+    W = L @ S @ L.T
+    assert rel(schur_blocks_solution(d["Q"], d["alpha"], d["beta"], W), kron_solve(A, W)) < 1e-11
+
+
+def test_bartels_stewart_normal_blocks_closed_form():
+    d = gen.normal_blocks(n=120, p=3, m=4)
+    A, L, S = d["A"], d["L"], d["S"]
+    W = L @ S @ L.T
+    X = O.bartels_stewart(A, W)
+    assert rel(X, schur_blocks_solution(d["Q"], d["alpha"], d["beta"], W)) < 1e-11
+
+
+def test_bartels_stewart_vs_lapack_routine():
+    d = gen.convdiff_shifted(grid=8, m=3)
+    A, L = d["A"], d["L"]
+    W = L @ L.T
+    X = O.bartels_stewart(A, W)
+    assert rel(X, sla.solve_continuous_lyapunov(A, -W)) < 1e-11
+
+
+def test_solution_symmetric_psd():
+    d = gen.convdiff_shifted(grid=6, m=2)
+    X = O.bartels_stewart(d["A"], d["L"] @ d["L"].T)
+    assert np.linalg.norm(X - X.T) <= 1e-12 * np.linalg.norm(X)
+    assert np.linalg.eigvalsh(0.5 * (X + X.T)).min() >= -1e-12 * np.linalg.norm(X, 2)
+
+
+# ------------------------------------------------------------- LU / rounding
+
+def test_getrf_pivots_match_lapack():
+    g = gen.rng(11)
+    A = g.standard_normal((40, 40))
+    LU, perm, ipiv = O.getrf_pp(A)
+    lu, piv = sla.lu_factor(A)
+    assert np.array_equal(ipiv, piv)
+    Lm = np.tril(LU, -1) + np.eye(40)
+    Um = np.triu(LU)
+    assert rel(Lm @ Um, A[perm]) < 1e-14
+
+
+def test_rounding_formats():
+    # bf16: 8-bit significand; 1 + 2^-8 is a tie -> even (1); 1 + 3*2^-8 -> 1 + 2^-6
+    x = np.array([1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, 1.0 + 2.0 ** -7, -3.0, 2.0 ** -130])
+    r = O.rnd(x, "bf16")
+    assert r[0] == 1.0 and r[1] == 1.0 + 2.0 ** -6 and r[2] == 1.0 + 2.0 ** -7 and r[3] == -3.0
+    # fp16: 11-bit significand, scaled into range: huge and tiny values keep 11 bits
+    y = np.array([1.0 + 2.0 ** -11, 1.0 + 2.0 ** -10, 3.0])
+    assert np.array_equal(O.rnd(y, "fp16"), [1.0, 1.0 + 2.0 ** -10, 3.0])
+    z = np.array([1e-12, 3e-12])
+    assert np.all(np.abs(O.rnd(z, "fp16") - z) <= 2.0 ** -11 * z)
+    w = np.array([1.0 + 2.0 ** -24, 1.0 + 2.0 ** -23])
+    assert np.array_equal(O.rnd(w, "fp32"), [1.0, 1.0 + 2.0 ** -23])
+    for k, u in O.UNIT.items():
+        assert abs(u - json.load(open(os.path.join(HERE, "golden", "table41_fp64_newton_counts.json")))
+                   ["unit_roundoff_table11"][k]) <= 0.005 * u
+
+
+# ----------------------------------------------------------- sign-Newton solver
+
+def test_sign_newton_converges_to_minus_identity():
+    d = gen.convdiff_shifted(grid=6, m=2)
+    rec = O.newton_sequence(d["A"], O.Opts(u_s="fp64"))
+    n = d["A"].shape[0]
+    assert np.linalg.norm(rec.A_final + np.eye(n), 1) < 1e-10
+
+
+def test_sign_newton_scaling_invariance():
+    # Frobenius scaling makes A_1 independent of a positive factor on A (Sec. 3): A -> 8 A.
+    d = gen.convdiff_shifted(grid=5, m=2)
+    r1 = O.newton_sequence(d["A"], O.Opts(u_s="fp64"))
+    r2 = O.newton_sequence(8.0 * d["A"], O.Opts(u_s="fp64"))
+    assert len(r1.inverses) == len(r2.inverses)
+    assert rel(r2.A_final, r1.A_final) < 1e-12
+    assert abs(r2.mus[0] * 8.0 - r1.mus[0]) < 1e-12 * r1.mus[0]
+
+
+def test_newton_chol_fp64_laplacian_config():
+    d = gen.fp64_laplacian(8, 2)
+    A, L = d["A"], d["L"]
+    W = L @ L.T
+    opts = O.Opts(u_s="fp64", scaling="det", newton_norm="fro", tau_newton=1e-12 * 64, rho=0.0,
+                  rank_tol=1e-14)
+    Z, rec = O.newton_chol(A, L, opts)
+    X = kron_solve(A, W)
+    assert rel(Z @ Z.T, X) < 1e-12
+    assert O.residual_eq41(A, Z, W) < 1e-14
+
+
+def test_newton_chol_fp64_kronecker_n16():
+    d = gen.fp64_laplacian(4, 2)
+    A, L = d["A"], d["L"]
+    opts = O.Opts(u_s="fp64", scaling="det", newton_norm="fro", tau_newton=1e-12 * 16, rho=0.0,
+                  rank_tol=1e-14)
+    Z, _ = O.newton_chol(A, L, opts)
+    assert rel(Z @ Z.T, kron_solve(A, L @ L.T)) < 1e-12
+
+
+def test_newton_ldlt_fp64_indefinite():
+    d = gen.normal_blocks(n=40, p=1, m=4)
+    A, L, S = d["A"], d["L"], d["S"]
+    s = np.diag(S)
+    Z, y, _ = O.newton_ldlt(A, L, s, O.Opts(u_s="fp64", rho=0.0))
+    X = kron_solve(A, L @ S @ L.T)
+    assert rel((Z * y) @ Z.T, X) < 1e-10
+
+
+def test_table41_fp64_iteration_counts():
+    gold = json.load(open(os.path.join(HERE, "golden", "table41_fp64_newton_counts.json")))
+    for nkey in ("100", "1000"):
+        n = int(nkey)
+        qs = gold["q"] if n == 100 else [0.1, 1.0, 2.0, 3.5]
+        for q in qs:
+            d = gen.paper_synthetic(n, q)
+            rec = O.newton_sequence(d["A"], O.Opts(u_s="fp64"))
+            want = gold["alpha"][nkey]["chol"][gold["q"].index(q)]
+            assert len(rec.inverses) == want, (n, q, len(rec.inverses), want)
+
+
+def test_table41_fp32_inner_counts_n100():
+    gold = json.load(open(os.path.join(HERE, "golden", "table41_fp64_newton_counts.json")))
+    g = gold["fp32_inner_iter_u64_n100_chol"]
+    for q, tot, al in zip(g["q"], g["total"], g["alpha"]):
+        d = gen.paper_synthetic(100, q)
+        Z, info = O.ir_chol(d["A"], d["L"], O.Opts(u_s="fp32"))
+        assert info.converged
+        assert (info.newton_total, info.newton_max) == (tot, al)
+
+
+def test_cond_column_is_lyapunov_kappa2():
+    # the printed cond 1.3e0 / 3.2e0 / 1.0e1 of Table 4.1 equals 10^q for the Sec. 4.2 generator
+    gold = json.load(open(os.path.join(HERE, "golden", "table41_fp64_newton_counts.json")))
+    for q, printed in zip(gold["q"], gold["cond_printed"]):
+        d = gen.paper_synthetic(100, q)
+        k = O.lyap_operator_kappa2_normal(-d["d"])
+        assert f"{k:.1e}".replace("e+0", "e").replace("e-0", "e-") == printed
+
+
+# -------------------------------------------------------- truncation routines
+
+def test_rank_trunc_chol_exact_rank_and_product():
+    g = gen.rng(5)
+    n, r = 80, 7
+    Z = g.standard_normal((n, r)) @ g.standard_normal((r, 30))  # exact rank 7, 30 columns
+    Zt = O.rank_trunc_chol(Z, 1e-10)
+    assert Zt.shape[1] == r
+    assert rel(Zt @ Zt.T, Z @ Z.T) < 1e-12
+
+
+def test_rank_trunc_chol_bound():
+    g = gen.rng(6)
+    n, c = 60, 25
+    U, _ = np.linalg.qr(g.standard_normal((n, c)))
+    s = 10.0 ** -np.linspace(0, 12, c)
+    Z = U * s
+    tol = 1e-6
+    Zt = O.rank_trunc_chol(Z, tol)
+    err = np.linalg.norm(Z @ Z.T - Zt @ Zt.T, 2)
+    assert err <= (tol * np.linalg.norm(Z, 2)) ** 2 * 1.0001 + 1e-15
+    assert Zt.shape[1] < c
+
+
+def test_rank_trunc_ldlt_indefinite():
+    g = gen.rng(8)
+    n = 50
+    Z = g.standard_normal((n, 4)) @ g.standard_normal((4, 12))
+    y = g.standard_normal(12)
+    Zt, yt = O.rank_trunc_ldlt(Z, y, 1e-12)
+    assert Zt.shape[1] == 4
+    assert np.any(yt < 0) or np.all(y > 0)
+    assert rel((Zt * yt) @ Zt.T, (Z * y) @ Z.T) < 1e-11
+
+
+# ---------------------------------------------- residual factorisation / update
+
+def test_res_fac_chol_norm_and_split():
+    d = gen.convdiff_shifted(grid=6, m=2)
+    A, L = d["A"], d["L"]
+    X = kron_solve(A, L @ L.T)
+    g = gen.rng(9)
+    Z = np.linalg.cholesky(X + 1e-6 * np.eye(36)) + 1e-4 * g.standard_normal((36, 36))
+    R = A @ Z @ Z.T + Z @ Z.T @ A.T + L @ L.T
+    Lp, Lm, resF = O.res_fac_chol(A, L, Z, 0.0)
+    assert abs(resF - np.linalg.norm(R)) < 1e-10 * np.linalg.norm(R)
+    assert rel(Lp @ Lp.T - Lm @ Lm.T, R) < 1e-10
+    # truncation at eta_r drops at most eta_r * ||R||_2 per eigenvalue
+    Lp2, Lm2, _ = O.res_fac_chol(A, L, Z, 1e-2)
+    err = np.linalg.norm(Lp2 @ Lp2.T - Lm2 @ Lm2.T - R, 2)
+    assert err <= 1.0001e-2 * np.linalg.norm(R, 2)
+
+
+def test_res_fac_ldlt_matches_explicit_residual():
+    d = gen.normal_blocks(n=30, p=1, m=3)
+    A, L, S = d["A"], d["L"], d["S"]
+    s = np.diag(S)
+    g = gen.rng(10)
+    Z = g.standard_normal((30, 9))
+    y = g.standard_normal(9)
+    R = A @ (Z * y) @ Z.T + (Z * y) @ Z.T @ A.T + L @ S @ L.T
+    Ld, sd, resF = O.res_fac_ldlt(A, L, s, Z, y, 0.0)
+    assert abs(resF - np.linalg.norm(R)) < 1e-10 * np.linalg.norm(R)
+    assert rel((Ld * sd) @ Ld.T, R) < 1e-10
+
+
+def test_sol_upt_chol_is_psd_projection():
+    g = gen.rng(12)
+    n = 40
+    Z = g.standard_normal((n, 6))
+    Zp = 0.1 * g.standard_normal((n, 3))
+    Zm = 0.3 * g.standard_normal((n, 2))
+    Xbp = Z @ Z.T + Zp @ Zp.T - Zm @ Zm.T
+    w, V = np.linalg.eigh(Xbp)
+    Xproj = (V * np.maximum(w, 0)) @ V.T
+    Zn = O.sol_upt_chol(Z, Zp, Zm, 1e-15)
+    assert rel(Zn @ Zn.T, Xproj) < 1e-12
+
+
+def test_sol_upt_ldlt_projection_and_indefinite():
+    g = gen.rng(13)
+    n = 40
+    Z = g.standard_normal((n, 5))
+    y = np.abs(g.standard_normal(5))
+    Zd = 0.2 * g.standard_normal((n, 4))
+    yd = g.standard_normal(4)
+    Xbp = (Z * y) @ Z.T + (Zd * yd) @ Zd.T
+    w, V = np.linalg.eigh(Xbp)
+    Zn, yn = O.sol_upt_ldlt(Z, y, Zd, yd, 1e-15, True)
+    assert rel((Zn * yn) @ Zn.T, (V * np.maximum(w, 0)) @ V.T) < 1e-12
+    Zi, yi = O.sol_upt_ldlt(Z, y, Zd, yd, 1e-15, False)
+    assert rel((Zi * yi) @ Zi.T, Xbp) < 1e-12
+
+
+def test_norm_xyx_gram_identity():
+    g = gen.rng(14)
+    Z = g.standard_normal((30, 7))
+    y = g.standard_normal(7)
+    assert abs(O.norm_xyx(Z, y) - np.linalg.norm((Z * y) @ Z.T)) < 1e-12 * np.linalg.norm((Z * y) @ Z.T)
+    assert abs(O.norm_xyx(Z) - np.linalg.norm(Z @ Z.T)) < 1e-12 * np.linalg.norm(Z @ Z.T)
+
+
+def test_residual_eq41_zero_at_solution():
+    d = gen.convdiff_shifted(grid=5, m=2)
+    A, L = d["A"], d["L"]
+    W = L @ L.T
+    X = kron_solve(A, W)
+    w, V = np.linalg.eigh(0.5 * (X + X.T))
+    Z = V * np.sqrt(np.maximum(w, 0))
+    assert O.residual_eq41(A, Z, W) < 1e-14
+
+
+# ------------------------------------------------------- refinement algorithms
+
+@pytest.mark.parametrize("us", ["fp64", "fp32", "fp16", "bf16"])
+def test_ir_chol_reaches_solution(us):
+    d = gen.paper_synthetic(60, 1.0)
+    A, L = d["A"], d["L"]
+    X = O.bartels_stewart(A, L @ L.T)
+    Z, info = O.ir_chol(A, L, O.Opts(u_s=us))
+    assert info.converged
+    assert O.residual_eq41(A, Z, L @ L.T) < 1e-13
+    assert rel(Z @ Z.T, X) < 1e-11
+    if us != "fp64":
+        assert info.ir_steps >= 1
+
+
+@pytest.mark.parametrize("us", ["fp64", "fp16"])
+def test_ir_ldlt_indefinite_reaches_solution(us):
+    d = gen.normal_blocks(n=40, p=1, m=4)
+    A, L, S = d["A"], d["L"], d["S"]
+    W = L @ S @ L.T
+    X = kron_solve(A, W)
+    Z, y, info = O.ir_ldlt(A, L, S, O.Opts(u_s=us))
+    assert info.converged
+    assert rel((Z * y) @ Z.T, X) < 1e-11
+
+
+def test_ir_stagnation_beyond_bf16_bound():
+    # kappa ~ 3e3 > 1e3 (Table 2.1 bound for bf16): refinement stalls and reports it
+    d = gen.paper_synthetic(100, 3.5)
+    Z, info = O.ir_chol(d["A"], d["L"], O.Opts(u_s="bf16"))
+    assert not info.converged
+
+
+# ---------------------------------------------------------------- adjoint
+
+def test_adjoint_vs_kronecker_bruteforce():
+    g = gen.rng(15)
+    n = 10
+    d = gen.random_stable(n, 2, g)
+    A, L = d["A"], d["L"]
+    C = g.standard_normal((3, n))
+    out = O.adjoint(A, L, C)
+    # d l / d vec(W) = -M^{-T} vec(G), M = I (x) A + A (x) I
+    I = np.eye(n)
+    M = np.kron(I, A) + np.kron(A, I)
+    Y = np.linalg.solve(M.T, -(C.T @ C).reshape(-1, order="F")).reshape(n, n, order="F")
+    assert rel(out["Y"], -Y) < 1e-11 or rel(out["Y"], Y) < 1e-11
+    assert rel(out["Y"], Y) < 1e-11
+
+
+def test_adjoint_vs_finite_differences():
+    g = gen.rng(16)
+    n = 12
+    d = gen.random_stable(n, 2, g)
+    A, L = d["A"], d["L"]
+    C = g.standard_normal((2, n))
+    out = O.adjoint(A, L, C)
+
+    def loss(Am, Lm):
+        X = kron_solve(Am, Lm @ Lm.T)
+        return float(np.trace(C @ X @ C.T))
+
+    for _ in range(3):
+        E = g.standard_normal((n, n))
+        E /= np.linalg.norm(E)
+        h = 1e-6 * np.linalg.norm(A)
+        fd = (loss(A + h * E, L) - loss(A - h * E, L)) / (2 * h)
+        assert abs(np.sum(out["dA"] * E) - fd) <= 1e-6 * abs(fd) + 1e-12
+        F = g.standard_normal(L.shape)
+        F /= np.linalg.norm(F)
+        h = 1e-6 * np.linalg.norm(L)
+        fd = (loss(A, L + h * F) - loss(A, L - h * F)) / (2 * h)
+        assert abs(np.sum(out["dL"] * F) - fd) <= 1e-6 * abs(fd) + 1e-12
+
+
+def test_adjoint_diagonal_closed_form():
+    g = gen.rng(17)
+    a = -10.0 ** g.uniform(-1, 1, 15)
+    C = g.standard_normal((2, 15))
+    L = g.standard_normal((15, 2))
+    out = O.adjoint(np.diag(a), L, C)
+    G = C.T @ C
+    assert rel(out["Y"], -G / (a[:, None] + a[None, :])) < 1e-12
