@@ -1,0 +1,195 @@
+/*
+ * liblyap -- mixed-precision iterative refinement for low-rank Lyapunov equations
+ *            A X + X A^T + W = 0,  W = L L^T  or  W = L S L^T           (Eq. (1.1), (1.2))
+ * on one NVIDIA GB300 GPU (sm_103a), after Benner & Liu, arXiv 2510.02126.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Matrices are column-major FP64 unless stated otherwise; `ld*` is the leading
+ *    dimension in elements (>= number of rows).
+ *  - Pointers named A, L, S, Z, D, Ainv, ... are DEVICE pointers (memory of the
+ *    GPU that is current when the context was created).  The caller owns every
+ *    buffer it passes; the library never frees or retains them after a call.
+ *  - Scalar outputs (rank_out, info, ...) are HOST pointers; they are written
+ *    after the call has synchronised its stream.
+ *  - All work is queued on the context's stream.  Device outputs are complete
+ *    when the entry point returns (every solver entry point synchronises the
+ *    stream, because its control flow depends on device-computed scalars).
+ *  - Return value: 0 = success, < 0 = error (LYAP_ERR_*), > 0 = warning (the
+ *    outputs hold the best result found).  lyap_last_error() gives detail.
+ *  - There is no CPU fallback: every arithmetic step runs in this library's
+ *    CUDA kernels.  A context on a machine without a usable GPU fails with
+ *    LYAP_ERR_CUDA.
+ *  - A context is not thread-safe; use one context per host thread / stream.
+ */
+#ifndef LIBLYAP_H
+#define LIBLYAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LYAP_OK 0
+#define LYAP_ERR_ARG (-1)        /* invalid argument (size, stride, null pointer, option) */
+#define LYAP_ERR_NONFINITE (-2)  /* NaN/Inf in an input or produced by the iteration */
+#define LYAP_ERR_SINGULAR (-3)   /* exactly zero pivot in an inversion */
+#define LYAP_ERR_NOCONV (-4)     /* sign-Newton reached kmax without meeting its stop test */
+#define LYAP_ERR_CAPACITY (-5)   /* output factor capacity too small; *rank_out = rank needed */
+#define LYAP_ERR_TIMEOUT (-6)    /* a bounded device wait gave up */
+#define LYAP_ERR_CUDA (-7)       /* CUDA runtime/driver error */
+#define LYAP_ERR_NOMEM (-8)      /* device workspace allocation failed */
+#define LYAP_WARN_STAGNATED 1    /* IR stopped by the stagnation rule, Eq. (4.2) */
+#define LYAP_WARN_MAXIT 2        /* IR reached imax without meeting tau_ir */
+
+/* Solver precisions u_s (Table 1.1); u = u_r = u_c = FP64 in this library. */
+typedef enum { LYAP_FP64 = 0, LYAP_FP32 = 1, LYAP_FP16 = 2, LYAP_BF16 = 3 } lyap_prec_t;
+
+/* Newton scaling (Sec. 3): Frobenius (the paper's choice, Sec. 4), determinantal, none. */
+typedef enum { LYAP_SCALE_FROB = 0, LYAP_SCALE_DET = 1, LYAP_SCALE_NONE = 2 } lyap_scaling_t;
+
+typedef struct lyap_ctx lyap_ctx_t;
+
+/*
+ * Algorithm parameters.  lyap_opts_default() sets the paper's values (Sec. 4.1):
+ * tau_ir = n u, imax = kmax = 50, rho = 0.1, eta_s = 10 u, eta_r = 1e-4,
+ * Frobenius scaling switched off once delta_k < 1e-2, stop test
+ * ||A_k + I||_1 <= 10 sqrt(n u_s) (Eq. (3.4)), stagnation theta > 0.9 twice (Eq. (4.2)).
+ */
+typedef struct {
+  int u_s;              /* lyap_prec_t: precision of the sign-Newton solver */
+  int scaling;          /* lyap_scaling_t */
+  double tau_newton;    /* <= 0: 10 sqrt(n u_s) */
+  int newton_norm_fro;  /* 0: ||A_k + I||_1 (Eq. (3.4)); 1: ||A_k + I||_F */
+  int stop_after;       /* the Newton loop ends at the stop_after-th iterate counted from,
+                           and including, the first one meeting the stop test ("two more
+                           iterations", Sec. 3.2; 2 reproduces Table 4.1's FP64 counts) */
+  int delta_rule;       /* 1: also stop on delta_k > delta_{k-1}/2 once unscaled (Sec. 4) */
+  double scale_off;     /* scaling is switched off for good once delta_k < scale_off (1e-2) */
+  double rank_tol;      /* <= 0: sqrt(u_s) (Cholesky type) / u_s (LDL^T type), relative */
+  double rho;           /* compress Z_k when cols(Z_k) > rho n; 0 = every step */
+  int kmax;             /* Newton iteration limit */
+  int imax;             /* refinement step limit */
+  double tau_ir;        /* <= 0: n * 2^-53; bound on the relative residual of Eq. (4.1) */
+  double eta_r;         /* residual truncation, relative to max |lambda(H)| */
+  double eta_s;         /* <= 0: 10 * 2^-53; solution truncation, relative to max |sigma(K)| */
+  double stag_theta;    /* stagnation ratio (0.9) */
+  int stag_count;       /* consecutive stagnating steps that stop IR (2) */
+  int project_psd;      /* 1: PSD projection in the solution update (forced off for indefinite S) */
+  int reserved[8];
+} lyap_opts_t;
+
+typedef struct {
+  int status;           /* same value as returned */
+  int rank;             /* columns of the returned factor */
+  int ir_steps;         /* refinement steps performed (corrections applied) */
+  int newton_calls;     /* calls of the sign-Newton solver (first solve + corrections) */
+  int newton_total;     /* total Newton iterations over all calls (varsigma, Table 4.1) */
+  int newton_max;       /* maximum Newton iterations in one call (alpha) */
+  int n_inversions;     /* distinct n x n inversions computed (stored and replayed, Sec. 3.4) */
+  int stagnated;        /* stagnation rule fired */
+  int converged;        /* relative residual <= tau_ir */
+  int n_res;            /* entries used in res_hist */
+  double res_final;     /* relative residual (Eq. (4.1)) of the returned factor */
+  double res_hist[64];  /* relative residual before each refinement step */
+  double mu[64];        /* Newton scaling parameters mu_0, mu_1, ... */
+  int64_t kernel_launches; /* CUDA kernels launched by this call */
+  double device_ms;     /* device time of the call (CUDA events on the context stream) */
+} lyap_info_t;
+
+/* Fill *o with the paper's defaults (u_s = FP16).  Returns LYAP_OK. */
+int lyap_opts_default(lyap_opts_t* o);
+
+/* Create a context bound to the current CUDA device and `stream` (a cudaStream_t,
+ * NULL = legacy default stream).  The context owns its device workspace and the
+ * stored inverse sequence; both grow on demand and are freed by lyap_ctx_destroy. */
+int lyap_ctx_create(lyap_ctx_t** ctx, void* stream);
+int lyap_ctx_destroy(lyap_ctx_t* ctx);
+/* Rebind the context to another stream (pending work is not synchronised). */
+int lyap_ctx_set_stream(lyap_ctx_t* ctx, void* stream);
+
+/*
+ * One sign-function Newton solve at precision opts->u_s (Sec. 3.2: the
+ * Cholesky-type iteration Eq. (3.2) when S == NULL, the LDL^T-type iteration
+ * Eq. (3.3) otherwise), with rank truncation (RankTruncChol / RankTruncLdlt).
+ *   A      n x n, lda >= n               (A must be Hurwitz)
+ *   L      n x m, ldl >= n
+ *   S      m x m symmetric, lds >= m, or NULL (W = L L^T)
+ *   Z      n x z_cap output, ldz >= n: X ~= Z Z^T (Cholesky) or Z diag(D) Z^T
+ *   D      z_cap output (LDL^T only; ignored when S == NULL; may be NULL then)
+ *   *rank_out  columns written to Z (on LYAP_ERR_CAPACITY: columns needed)
+ * The computed inverse sequence {A_k^{-1}, mu_k} is kept in the context (Sec. 3.4).
+ */
+int lyap_sign_solve(lyap_ctx_t* ctx, const double* A, int64_t n, int64_t lda,
+                    const double* L, int64_t ldl, int64_t m, const double* S, int64_t lds,
+                    const lyap_opts_t* opts, double* Z, int64_t ldz, int64_t z_cap,
+                    double* D, int64_t* rank_out, lyap_info_t* info);
+
+/*
+ * Mixed-precision iterative refinement: Algorithm IR-Chol (Sec. 2.1) when S == NULL,
+ * Algorithm IR-LDLT (Sec. 2.3) otherwise, with the sign-Newton solver at u_s,
+ * the residual factorisation (Fragments ResFacChol / ResFacLdlt) and the projected
+ * solution update (Fragments SolUptChol / SolUptLdlt) in FP64, and the stopping
+ * rules of Sec. 4.1.  Every correction solve replays the stored inverse sequence
+ * of the first solve (Sec. 3.4).  Arguments as for lyap_sign_solve.
+ */
+int lyap_solve_ir(lyap_ctx_t* ctx, const double* A, int64_t n, int64_t lda,
+                  const double* L, int64_t ldl, int64_t m, const double* S, int64_t lds,
+                  const lyap_opts_t* opts, double* Z, int64_t ldz, int64_t z_cap,
+                  double* D, int64_t* rank_out, lyap_info_t* info);
+
+/*
+ * Relative residual of Eq. (4.1),
+ *   ||A X + X A^T + W||_F / (||W||_F + 2 ||X||_F ||A||_F),  X = Z Z^T or Z diag(D) Z^T,
+ * evaluated in FP64 from the factors without forming n x n matrices (thin QR of
+ * [Z, AZ, L] and the Frobenius norm of the small core, as in Fragment ResFacChol).
+ * D == NULL means X = Z Z^T; S == NULL means W = L L^T.  *res_out is a host double.
+ */
+int lyap_residual(lyap_ctx_t* ctx, const double* A, int64_t n, int64_t lda,
+                  const double* L, int64_t ldl, int64_t m, const double* S, int64_t lds,
+                  const double* Z, int64_t ldz, int64_t r, const double* D, double* res_out);
+
+/*
+ * Dense inversion behind every Newton step (Sec. 3.3 cost model: 2 n^3 flops):
+ * blocked Gauss-Jordan elimination with partial pivoting -- the getrf pivot
+ * sequence (largest |a_ij| in the active column, lowest row on ties) fused with
+ * the getri inversion -- at precision `prec` (FP64 / FP32 SIMT, FP16 / BF16
+ * operands on tcgen05 tensor cores with FP32 accumulation and an FP32 working matrix).
+ *   Ainv   n x n output, ldai >= n (may not alias A)
+ *   ipiv   optional DEVICE int32[n]: row chosen as pivot at step j (0-based), or NULL
+ *   logabsdet optional HOST double: log|det A| from the pivots, or NULL
+ */
+int lyap_invert(lyap_ctx_t* ctx, const double* A, int64_t n, int64_t lda, int prec,
+                double* Ainv, int64_t ldai, int32_t* ipiv, double* logabsdet);
+
+/*
+ * RankTruncChol (Sec. 3.2): QR with column pivoting of Z^T, truncated at the first
+ * r with ||S_r||_F <= tol * |r_11|, returned as Pi [T C]^T (n x r), overwriting the
+ * leading r columns of Z (FP64 arithmetic).  *rank_out receives r.
+ */
+int lyap_rank_trunc(lyap_ctx_t* ctx, double* Z, int64_t n, int64_t c, int64_t ldz, double tol,
+                    int64_t* rank_out);
+
+/*
+ * Symmetric eigendecomposition H = Q diag(w) Q^T of a q x q FP64 matrix (the kernel
+ * behind Fragments ResFacChol / SolUptChol): H (ldh >= q, overwritten), w (q, ascending),
+ * Q (q x q, ldq >= q).  All device pointers.  fp64_refine = 1 refines the eigenpairs
+ * to FP64 accuracy; 0 returns the FP32-accurate result.
+ */
+int lyap_sym_eig(lyap_ctx_t* ctx, double* H, int64_t q, int64_t ldh, double* w, double* Q,
+                 int64_t ldq, int fp64_refine);
+
+/* Message of the last error raised in this process (static storage). */
+const char* lyap_last_error(void);
+/* Human-readable name of a status code. */
+const char* lyap_status_string(int status);
+/* Library version string. */
+const char* lyap_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIBLYAP_H */

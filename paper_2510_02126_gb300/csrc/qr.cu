@@ -1,0 +1,314 @@
+// Householder QR kernels.  Both factorisations are cooperative launches: the
+// columns are distributed cyclically over the CTAs (one warp per column at a
+// time) and the CTAs meet at a bounded grid barrier between reflectors, so the
+// FP64 arithmetic of the trailing updates runs on many SMs at once.
+#include "qr.cuh"
+
+namespace lyap {
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  T t = (lane < nw) ? red[lane] : T(0);
+  t = warp_sum(t);
+  return t;  // valid in every warp
+}
+
+// ---------------------------------------------------------------------------
+// thin Householder QR (cooperative)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+hqr_kernel(T* __restrict__ F, int64_t m, int64_t q, int64_t ld, T* __restrict__ tau, GridBar* bar,
+           int* status) {
+  __shared__ T red[32];
+  const int G = gridDim.x, b = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t kmax = (m < q) ? m : q;
+  for (int64_t j = 0; j < kmax; ++j) {
+    if ((j % G) == b) {
+      // reflector of column j (this block owns it and has applied H_0..H_{j-1} to it)
+      T* x = F + j + j * ld;
+      T sig = T(0);
+      for (int64_t i = 1 + threadIdx.x; i < m - j; i += blockDim.x) sig = fma(x[i], x[i], sig);
+      sig = block_sum(sig, red);
+      const T alpha = x[0];
+      T beta, tj, scale;
+      if (sig == T(0)) {
+        tj = T(0);
+        beta = alpha;
+        scale = T(0);
+      } else {
+        const T nrm = sqrt(alpha * alpha + sig);
+        beta = (alpha <= T(0)) ? nrm : -nrm;
+        tj = (beta - alpha) / beta;
+        scale = T(1) / (alpha - beta);
+      }
+      __syncthreads();
+      for (int64_t i = 1 + threadIdx.x; i < m - j; i += blockDim.x) x[i] *= scale;
+      if (threadIdx.x == 0) { x[0] = beta; tau[j] = tj; }
+    }
+    if (!grid_sync(bar, status)) return;
+    // apply H_j to owned columns l > j, one warp per column
+    const T tj = tau[j];
+    const T* v = F + j + j * ld;  // v[0] = 1 implicit
+    int slot = 0;
+    for (int64_t l = b; l < q; l += G) {
+      if (l <= j) continue;
+      if ((slot++ % nw) != warp) continue;
+      T* y = F + j + l * ld;
+      T w = T(0);
+      for (int64_t i = 1 + lane; i < m - j; i += 32) w = fma(v[i], y[i], w);
+      w = warp_sum(w) + y[0];
+      w *= tj;
+      if (lane == 0) y[0] -= w;
+      for (int64_t i = 1 + lane; i < m - j; i += 32) y[i] = fma(-w, v[i], y[i]);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+int householder_qr(T* F, int64_t m, int64_t q, int64_t ld, T* tau, QRScratch& sc, cudaStream_t s) {
+  if (m <= 0 || q <= 0) return LYAP_OK;
+  int G = (int)std::min<int64_t>(q, sc.num_sms);
+  if (G < 1) G = 1;
+  LYAP_CUDA_TRY(cudaMemsetAsync(sc.bar, 0, sizeof(GridBar), s));
+  void* args[] = {&F, &m, &q, &ld, &tau, &sc.bar, &sc.status};
+  LYAP_CUDA_TRY(cudaLaunchCooperativeKernel((void*)hqr_kernel<T>, dim3(G), dim3(256), args, 0, s));
+  lyap_count_launch();
+  return LYAP_OK;
+}
+template int householder_qr<float>(float*, int64_t, int64_t, int64_t, float*, QRScratch&, cudaStream_t);
+template int householder_qr<double>(double*, int64_t, int64_t, int64_t, double*, QRScratch&, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Y = H_0 ... H_{k-1} [C; 0]: each column of Y is independent, one warp each
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(32)
+apply_q_kernel(const T* __restrict__ F, int64_t m, int64_t k, int64_t ldf, const T* __restrict__ tau,
+               const T* __restrict__ C, int64_t ldc, int64_t r, T* __restrict__ Y, int64_t ldy) {
+  const int64_t col = blockIdx.x;
+  if (col >= r) return;
+  const int lane = threadIdx.x;
+  T* y = Y + col * ldy;
+  for (int64_t i = lane; i < m; i += 32) y[i] = (i < k) ? C[i + col * ldc] : T(0);
+  __syncwarp();
+  for (int64_t j = k - 1; j >= 0; --j) {
+    const T* v = F + j + j * ldf;
+    T* yj = y + j;
+    T w = T(0);
+    for (int64_t i = 1 + lane; i < m - j; i += 32) w = fma(v[i], yj[i], w);
+    w = warp_sum(w) + yj[0];
+    w *= tau[j];
+    __syncwarp();
+    if (lane == 0) yj[0] -= w;
+    for (int64_t i = 1 + lane; i < m - j; i += 32) yj[i] = fma(-w, v[i], yj[i]);
+    __syncwarp();
+  }
+}
+
+template <typename T>
+int apply_q(const T* F, int64_t m, int64_t k, int64_t ldf, const T* tau, const T* C, int64_t ldc,
+            int64_t r, T* Y, int64_t ldy, cudaStream_t s) {
+  if (r <= 0 || m <= 0) return LYAP_OK;
+  apply_q_kernel<T><<<(unsigned)r, 32, 0, s>>>(F, m, k, ldf, tau, C, ldc, r, Y, ldy);
+  LYAP_CUDA_TRY(cudaGetLastError());
+  lyap_count_launch();
+  return LYAP_OK;
+}
+template int apply_q<float>(const float*, int64_t, int64_t, int64_t, const float*, const float*, int64_t,
+                            int64_t, float*, int64_t, cudaStream_t);
+template int apply_q<double>(const double*, int64_t, int64_t, int64_t, const double*, const double*, int64_t,
+                             int64_t, double*, int64_t, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// QR with column pivoting of M = Z^T (c x n); columns of M = rows of Z
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+qrcp_kernel(T* __restrict__ Z, int64_t n, int64_t c, int64_t ldz, double tol, T* __restrict__ M,
+            T* __restrict__ nrm, T* __restrict__ nrm_ref, int* __restrict__ piv, T* __restrict__ rdiag,
+            double* __restrict__ cand, int* __restrict__ rank_out, GridBar* bar, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* v = reinterpret_cast<T*>(smem_raw);  // reflector, length c
+  __shared__ T red[32];
+  __shared__ double redd[32];
+  __shared__ int redi[32];
+  __shared__ double r11_s;
+  const int G = gridDim.x, b = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+
+  // copy-in: M[:, i] = Z[i, :], norms, identity pivots (owned columns i = b mod G)
+  for (int64_t i = b; i < n; i += G) {
+    T acc = T(0);
+    for (int64_t l = threadIdx.x; l < c; l += blockDim.x) {
+      const T z = Z[i + l * ldz];
+      M[l + i * c] = z;
+      acc = fma(z, z, acc);
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) { nrm[i] = acc; nrm_ref[i] = acc; piv[i] = (int)i; }
+  }
+  const int64_t kmax = (c < n) ? c : n;
+  int64_t r = kmax;
+  for (int64_t j = 0; j < kmax; ++j) {
+    // (1) local argmax and tail sum over owned columns i >= j
+    double bv = -1.0, ts = 0.0;
+    int bi = -1;
+    for (int64_t i = b + (int64_t)threadIdx.x * G; i < n; i += (int64_t)blockDim.x * G) {
+      if (i < j) continue;
+      const double w = (double)nrm[i];
+      ts += w;
+      if (bi < 0 || w > bv) { bv = w; bi = (int)i; }
+    }
+    warp_argmax(bv, bi);
+    ts = warp_sum(ts);
+    __syncthreads();
+    if (lane == 0) { redd[warp] = bv; redi[warp] = bi; }
+    __syncthreads();
+    if (warp == 0) {
+      double v2 = (lane < nw) ? redd[lane] : -1.0;
+      int i2 = (lane < nw) ? redi[lane] : -1;
+      warp_argmax(v2, i2);
+      if (lane == 0) { cand[3 * b] = v2; cand[3 * b + 1] = (double)i2; }
+    }
+    __syncthreads();
+    if (lane == 0) redd[warp] = ts;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < nw; ++w) t += redd[w];
+      cand[3 * b + 2] = t;
+    }
+    if (!grid_sync(bar, status)) return;
+    // (2) global pivot + truncation test (identical in every block)
+    double pv = -1.0, tail = 0.0;
+    int p = -1;
+    for (int e = lane; e < G; e += 32) {
+      const double cv = cand[3 * e];
+      const int ci = (int)cand[3 * e + 1];
+      if (ci >= 0 && (p < 0 || cv > pv || (cv == pv && ci < p))) { pv = cv; p = ci; }
+    }
+    warp_argmax(pv, p);
+    if (threadIdx.x < 32) {
+      double t = 0.0;
+      for (int e = lane; e < G; e += 32) t += cand[3 * e + 2];
+      t = warp_sum(t);
+      if (threadIdx.x == 0) redd[0] = t;
+    }
+    __syncthreads();
+    tail = redd[0];
+    __syncthreads();
+    if (j == 0 && !(tail > 0.0)) { r = 0; break; }
+    if (j >= 1 && sqrt(fmax(tail, 0.0)) <= tol * r11_s) { r = j; break; }
+    // (3) swap columns j <-> p (block 0), then everybody reads column j
+    if (b == 0 && p != (int)j) {
+      for (int64_t l = threadIdx.x; l < c; l += blockDim.x) {
+        const T a = M[l + j * c];
+        M[l + j * c] = M[l + (int64_t)p * c];
+        M[l + (int64_t)p * c] = a;
+      }
+      if (threadIdx.x == 0) {
+        T t = nrm[j]; nrm[j] = nrm[p]; nrm[p] = t;
+        t = nrm_ref[j]; nrm_ref[j] = nrm_ref[p]; nrm_ref[p] = t;
+        const int q = piv[j]; piv[j] = piv[p]; piv[p] = q;
+      }
+    }
+    if (!grid_sync(bar, status)) return;
+    // (4) reflector from column j (computed redundantly, kept in shared memory)
+    const T* x = M + j + j * c;
+    T sig = T(0);
+    for (int64_t l = 1 + threadIdx.x; l < c - j; l += blockDim.x) sig = fma(x[l], x[l], sig);
+    sig = block_sum(sig, red);
+    const T alpha = x[0];
+    T beta, tj, scale;
+    if (sig == T(0)) { beta = alpha; tj = T(0); scale = T(0); }
+    else {
+      const T nrmx = sqrt(alpha * alpha + sig);
+      beta = (alpha <= T(0)) ? nrmx : -nrmx;
+      tj = (beta - alpha) / beta;
+      scale = T(1) / (alpha - beta);
+    }
+    for (int64_t l = 1 + threadIdx.x; l < c - j; l += blockDim.x) v[l] = x[l] * scale;
+    if (threadIdx.x == 0) {
+      v[0] = T(1);
+      if (j == 0) r11_s = fabs((double)beta);
+      if (b == 0) rdiag[j] = beta;
+    }
+    __syncthreads();
+    // (5) apply to owned columns i > j (one warp per column) + norm downdate
+    int slot = 0;
+    for (int64_t i = b; i < n; i += G) {
+      if (i <= j) continue;
+      if ((slot++ % nw) != warp) continue;
+      T* y = M + j + i * c;
+      T w = T(0);
+      for (int64_t l = 1 + lane; l < c - j; l += 32) w = fma(v[l], y[l], w);
+      w = (warp_sum(w) + y[0]) * tj;
+      const T top = y[0] - w;
+      T tail2 = T(0);
+      for (int64_t l = 1 + lane; l < c - j; l += 32) {
+        const T nv = fma(-w, v[l], y[l]);
+        y[l] = nv;
+        tail2 = fma(nv, nv, tail2);
+      }
+      if (lane == 0) y[0] = top;
+      // downdate ||M[j+1:, i]||^2 ; recompute when cancellation is severe
+      T nn = nrm[i] - top * top;
+      const T eps = (sizeof(T) == 8) ? T(1.5e-8) : T(3.5e-4);  // ~ sqrt(machine eps)
+      if (!(nn > eps * nrm_ref[i])) {
+        nn = warp_sum(tail2);
+        if (lane == 0) nrm_ref[i] = nn;
+      }
+      if (lane == 0) nrm[i] = (nn > T(0)) ? nn : T(0);
+    }
+    __syncthreads();
+  }
+  if (!grid_sync(bar, status)) return;
+  // (6) output: Z[piv[i], l] = R[l, i] for l < r
+  for (int64_t i = b; i < n; i += G) {
+    const int pi = piv[i];
+    for (int64_t l = threadIdx.x; l < r; l += blockDim.x) {
+      T val;
+      if (l < i) val = M[l + i * c];
+      else if (l == i) val = rdiag[i];
+      else val = T(0);
+      Z[pi + l * ldz] = val;
+    }
+  }
+  if (b == 0 && threadIdx.x == 0) *rank_out = (int)r;
+}
+
+template <typename T>
+int qrcp_truncate(T* Z, int64_t n, int64_t c, int64_t ldz, double tol, QRScratch& sc, cudaStream_t s) {
+  if (n <= 0 || c <= 0) {
+    LYAP_CUDA_TRY(cudaMemsetAsync(sc.rank, 0, sizeof(int), s));
+    return LYAP_OK;
+  }
+  int G = (int)std::min<int64_t>(ceil_div(n, 8), sc.num_sms);
+  G = std::min(G, 256);
+  if (G < 1) G = 1;
+  const size_t smem = sizeof(T) * (size_t)c;
+  auto kern = qrcp_kernel<T>;
+  if (smem > 48 * 1024) LYAP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LYAP_CUDA_TRY(cudaMemsetAsync(sc.bar, 0, sizeof(GridBar), s));
+  T* M = (T*)sc.work;
+  T* nrm = (T*)sc.norms;
+  T* nrm_ref = nrm + n;
+  T* rdiag = (T*)sc.rdiag;
+  double* cand = (double*)sc.cand;
+  void* args[] = {&Z, &n, &c, &ldz, &tol, &M, &nrm, &nrm_ref, &sc.piv, &rdiag, &cand, &sc.rank, &sc.bar, &sc.status};
+  LYAP_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3(G), dim3(256), args, smem, s));
+  lyap_count_launch();
+  return LYAP_OK;
+}
+template int qrcp_truncate<float>(float*, int64_t, int64_t, int64_t, double, QRScratch&, cudaStream_t);
+template int qrcp_truncate<double>(double*, int64_t, int64_t, int64_t, double, QRScratch&, cudaStream_t);
+
+}  // namespace lyap

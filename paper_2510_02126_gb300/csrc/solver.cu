@@ -1,0 +1,1411 @@
+// Host driver and C-ABI of liblyap: the sign-function Newton solver (Sec. 3) and
+// mixed-precision iterative refinement (Sec. 2) on one GPU.  Every arithmetic
+// step runs in this library's kernels; the host only sequences launches and
+// reads back the device-computed scalars that steer the loops.
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "dense.cuh"
+#include "eig.cuh"
+#include "gj_inverse.cuh"
+#include "qr.cuh"
+#include "tc_gemm.cuh"
+
+// ---------------------------------------------------------------------------
+// process-wide diagnostics
+// ---------------------------------------------------------------------------
+static char g_err[512] = "";
+static int64_t g_launches = 0;
+
+void lyap_set_error_message(const char* what, const char* file, int line) {
+  snprintf(g_err, sizeof(g_err), "%s (%s:%d)", what, file, line);
+}
+void lyap_count_launch(int k) { g_launches += k; }
+
+namespace lyap {
+
+struct Buf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+static int ensure(Buf& b, size_t bytes) {
+  if (bytes <= b.cap && b.p) return LYAP_OK;
+  if (b.p) {
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  size_t want = bytes + bytes / 4 + 256;
+  if (cudaMalloc(&b.p, want) != cudaSuccess) {
+    cudaGetLastError();
+    lyap_set_error_message("device allocation failed", __FILE__, __LINE__);
+    return LYAP_ERR_NOMEM;
+  }
+  b.cap = want;
+  return LYAP_OK;
+}
+template <typename T>
+static T* P(Buf& b) { return reinterpret_cast<T*>(b.p); }
+
+// Device-side state of one sign-Newton run (read back by the host after each step).
+struct NewtonState {
+  double ssA, ssX, maxX, mu, ssA1, ssD, ssE, stopv, delta, delta_prev, logdet;
+  double meas[64];
+  int scaling_on, fired, prev_unscaled, done, k, eX, status, pad;
+};
+
+}  // namespace lyap
+
+struct lyap_ctx {
+  int device = 0;
+  cudaStream_t s = nullptr;
+  int num_sms = 0;
+  lyap::Buf state, scal, part, hist;
+  // inversion
+  lyap::GJWork gj;
+  lyap::Buf gjM0, gjM1, gjPp, gjRt, gjOrig, gjPerm0, gjPerm1, gjLog, gjIpiv, gjStatus, gjExps, gjAmax;
+  // Newton working buffers
+  lyap::Buf A0, A1, pinv, colsum, Zw, Zw2, Zh, eZ, yv, yv2;
+  // stored inverse sequence (Sec. 3.4)
+  lyap::Buf store, dmu, dex;
+  int store_n = 0, store_prec = -1, store_count = 0, store_e0 = 0;
+  size_t store_elt = 0;
+  int64_t store_ld = 0;  // row pitch (elements) of a stored inverse
+  // FP64 refinement buffers
+  lyap::Buf F, tau, Tm, TP, H, w, Qh, Csel, Lp, Lm, Zs, Zbest, G, gram, ysol, ybest, ytmp, Lw, Sd, Vs, Lst;
+  // scratch of the QR and eigen kernels
+  lyap::QRScratch qr;
+  lyap::Buf qrBar, qrStatus, qrCand, qrNorms, qrPiv, qrRdiag, qrWork, qrRank;
+  lyap::EigScratch eig;
+  lyap::Buf eigWork32, eigX, eigR, eigS, eigHX, eigE, eigLam, eigRed, eigW, eigPv, eigInt;
+  void* hpin = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
+namespace lyap {
+
+using Ctx = lyap_ctx;
+
+static bool is16(int prec) { return prec == LYAP_FP16 || prec == LYAP_BF16; }
+
+// ---------------------------------------------------------------------------
+// small kernels of the Newton step (Eq. (3.1a)-(3.3))
+// ---------------------------------------------------------------------------
+__global__ void iota_kernel(int* p, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = i;
+}
+__global__ void pinv_kernel(const int* __restrict__ perm, int* __restrict__ pinv, int n) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) pinv[perm[c]] = c;
+}
+
+__global__ void newton_init_kernel(NewtonState* st, int scaling) {
+  st->scaling_on = (scaling != LYAP_SCALE_NONE);
+  st->fired = 0;
+  st->prev_unscaled = 0;
+  st->done = 0;
+  st->k = 0;
+  st->eX = 0;
+  st->status = 0;
+  st->delta_prev = -1.0;
+  st->mu = 1.0;
+}
+
+// mu_k (Frobenius: (||A^-1||_F/||A||_F)^{1/2}; determinantal: |det A|^{-1/n} from the
+// pivots in logarithms; 1 once scaling is off) and the storage exponent of A_k^{-1}.
+__global__ void newton_mu_kernel(NewtonState* st, int n, int scaling, int store16) {
+  double mu = 1.0;
+  if (st->scaling_on) {
+    if (scaling == LYAP_SCALE_FROB) mu = sqrt(sqrt(st->ssX) / sqrt(st->ssA));
+    else if (scaling == LYAP_SCALE_DET) mu = exp(-st->logdet / (double)n);
+  }
+  if (!isfinite(mu) || !(mu > 0.0) || !isfinite(st->ssX)) atomicCAS(&st->status, 0, LYAP_ERR_NONFINITE);
+  st->mu = mu;
+  st->eX = store16 ? pow2_exponent(st->maxX) : 0;
+}
+
+// A_{k+1} = (mu A_k + mu^{-1} A_k^{-1}) / 2 with A_k^{-1}[i, j] = X[i, pinv[j]];
+// also stores A_k^{-1} (scaled by 2^-eX) and the partial sums of
+// ||A_{k+1}||_F^2, ||A_{k+1} - A_k||_F^2 and ||A_{k+1} + I||_F^2.
+template <typename T, typename ST>
+__global__ void __launch_bounds__(256)
+newton_update_kernel(int n, const T* __restrict__ Ak, const T* __restrict__ X, const int* __restrict__ pinv,
+                     const NewtonState* __restrict__ st, T* __restrict__ An, ST* __restrict__ Xs, int64_t ldx,
+                     double* __restrict__ part) {
+  const double mu = st->mu, imu = 1.0 / st->mu;
+  const double sx = ldexp(1.0, -st->eX);
+  const int64_t total = (int64_t)n * n;
+  double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, j = e - i * n;
+    const double x = (double)X[i * n + pinv[j]];
+    const double a = (double)Ak[e];
+    const double an_d = 0.5 * (mu * a + imu * x);
+    const T an = (T)an_d;
+    An[e] = an;
+    Xs[i * ldx + j] = (ST)(x * sx);
+    const double av = (double)an;
+    s1 = fma(av, av, s1);
+    const double d = av - a;
+    s2 = fma(d, d, s2);
+    const double ep = av + (i == j ? 1.0 : 0.0);
+    s3 = fma(ep, ep, s3);
+  }
+  __shared__ double sh[3][8];
+  s1 = warp_sum(s1);
+  s2 = warp_sum(s2);
+  s3 = warp_sum(s3);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) { sh[0][warp] = s1; sh[1][warp] = s2; sh[2][warp] = s3; }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += sh[threadIdx.x][w];
+    part[threadIdx.x * RED_BLOCKS + blockIdx.x] = t;
+  }
+}
+__global__ void newton_sums_kernel(const double* __restrict__ part, int nb, NewtonState* st) {
+  // fixed-order sums of the three partial vectors
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w < 3) {
+    double t = 0.0;
+    for (int i = lane; i < nb; i += 32) t += part[w * RED_BLOCKS + i];
+    t = warp_sum(t);
+    if (lane == 0) {
+      if (w == 0) st->ssA1 = t;
+      else if (w == 1) st->ssD = t;
+      else st->ssE = t;
+    }
+  }
+}
+// column sums of |A + I| (row-major A) -> colsum[j]
+template <typename T>
+__global__ void colsum_kernel(int n, const T* __restrict__ A, double* __restrict__ colsum) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    double t = 0.0;
+    for (int i = 0; i < n; ++i) t += fabs((double)A[(int64_t)i * n + j] + (i == j ? 1.0 : 0.0));
+    colsum[j] = t;
+  }
+}
+// stop test of Eq. (3.4) (or the Frobenius variant), Higham's delta rule, scaling switch-off
+__global__ void newton_test_kernel(NewtonState* st, double tau, int norm_fro, int stop_after, int delta_rule,
+                                   double scale_off, double* dmu, int* dex, int kidx) {
+  const double delta = sqrt(st->ssD) / sqrt(st->ssA1);
+  const double meas = norm_fro ? sqrt(st->ssE) : st->stopv;
+  const int unscaled = (st->mu == 1.0);
+  if (st->fired == 0) {
+    bool fire = meas <= tau;
+    if (delta_rule && unscaled && st->prev_unscaled && st->delta_prev >= 0.0 && delta > 0.5 * st->delta_prev)
+      fire = true;
+    if (fire) st->fired = 1;
+  } else {
+    st->fired += 1;
+  }
+  st->done = (st->fired >= (stop_after > 1 ? stop_after : 1));
+  if (st->scaling_on && delta < scale_off) st->scaling_on = 0;
+  st->delta = delta;
+  st->delta_prev = delta;
+  st->prev_unscaled = unscaled;
+  st->ssA = st->ssA1;
+  if (kidx < 64) st->meas[kidx] = meas;
+  dmu[kidx] = st->mu;
+  dex[kidx] = st->eX;
+  st->k = kidx + 1;
+  if (!isfinite(meas) || !isfinite(delta)) atomicCAS(&st->status, 0, LYAP_ERR_NONFINITE);
+}
+__global__ void sum_vec_kernel(const double* __restrict__ v, int n, double* out) {
+  double t = 0.0;
+  for (int i = threadIdx.x; i < n; i += 32) t += v[i];
+  t = warp_sum(t);
+  if (threadIdx.x == 0) *out = t;
+}
+// Cholesky type (Eq. (3.2)):  Z[:, :c] *= sqrt(mu/2),  Z[:, c:2c] *= 1/sqrt(2 mu)
+// LDL^T type (Eq. (3.3)):    y[c + j] = y[j] / (2 mu),  y[j] *= mu / 2
+template <typename T>
+__global__ void factor_scale_kernel(T* __restrict__ Z, int64_t ld, int n, int c, const double* __restrict__ mu_p,
+                                    int ldlt, double* __restrict__ y) {
+  const double mu = *mu_p;
+  if (!ldlt) {
+    const double a = sqrt(0.5 * mu), b = 1.0 / sqrt(2.0 * mu);
+    const int64_t total = (int64_t)n * 2 * c;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t j = e / n, i = e - j * n;
+      Z[i + j * ld] = (T)((double)Z[i + j * ld] * (j < c ? a : b));
+    }
+  } else if (blockIdx.x == 0) {
+    for (int j = threadIdx.x; j < c; j += blockDim.x) {
+      const double yj = y[j];
+      y[c + j] = yj / (2.0 * mu);
+      y[j] = 0.5 * mu * yj;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// small kernels of the refinement (Fragments ResFac*/SolUpt*)
+// ---------------------------------------------------------------------------
+// Tm (kr x q) = upper trapezoid of F's leading rows
+__global__ void extract_r_kernel(const double* __restrict__ F, int64_t ldf, int kr, int q, double* __restrict__ Tm) {
+  const int64_t total = (int64_t)kr * q;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / kr, i = e - j * kr;
+    Tm[i + j * kr] = (i <= j) ? F[i + j * ldf] : 0.0;
+  }
+}
+// TP = T * middle, middle = [[0, Y, 0], [Y, 0, 0], [0, 0, S]] (Y = diag(y) or I, S = diag(sd) or I)
+__global__ void core_right_kernel(const double* __restrict__ Tm, int kr, int c, int m, const double* __restrict__ y,
+                                  const double* __restrict__ sd, double* __restrict__ TP) {
+  const int q = 2 * c + m;
+  const int64_t total = (int64_t)kr * q;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / kr, i = e - j * kr;
+    double v;
+    if (j < c) v = Tm[i + (j + c) * kr] * (y ? y[j] : 1.0);
+    else if (j < 2 * c) v = Tm[i + (j - c) * kr] * (y ? y[j - c] : 1.0);
+    else v = Tm[i + j * kr] * (sd ? sd[j - 2 * c] : 1.0);
+    TP[i + j * kr] = v;
+  }
+}
+// Gamma * J with J = diag(sign) (SolUptChol: +1 for Z, Z+, -1 for Z-) or diag(ups) (SolUptLdlt)
+__global__ void scale_cols_dev_kernel(const double* __restrict__ A, int kr, int q, int cneg_start,
+                                      const double* __restrict__ d, double* __restrict__ B) {
+  const int64_t total = (int64_t)kr * q;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / kr, i = e - j * kr;
+    double f = d ? d[j] : (j >= cneg_start ? -1.0 : 1.0);
+    B[i + j * kr] = A[i + j * kr] * f;
+  }
+}
+// Ranges of an ascending spectrum w[0..q): out[0] = #(w <= -thr), out[1] = first index with w >= thr,
+// thr = eta * max|w|.  Also out[2] = first index with |w| > thr (magnitude mode helper not needed).
+__global__ void select_kernel(const double* __restrict__ w, int q, double eta, int strict, int* __restrict__ out,
+                              double* __restrict__ thr_out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double mx = 0.0;
+  for (int i = 0; i < q; ++i) mx = fmax(mx, fabs(w[i]));
+  const double thr = eta * mx;
+  int nneg = 0;
+  while (nneg < q && (strict ? (w[nneg] < -thr) : (w[nneg] <= -thr))) ++nneg;
+  int pos = q;
+  while (pos > 0 && (strict ? (w[pos - 1] > thr) : (w[pos - 1] >= thr))) --pos;
+  if (!(mx > 0.0)) { nneg = 0; pos = q; }
+  if (pos < nneg) pos = nneg;
+  out[0] = nneg;
+  out[1] = pos;
+  *thr_out = thr;
+}
+// C[:, t] = Q[:, i0 + t] * f(w[i0 + t]), f = sqrt(|w|) (Cholesky types) or 1 (LDL^T, value copied to yo)
+__global__ void gather_cols_kernel(const double* __restrict__ Q, int64_t ldq, int kr, const double* __restrict__ w,
+                                   int i0, int cnt, int use_sqrt, double* __restrict__ C, int64_t ldc,
+                                   double* __restrict__ yo) {
+  const int64_t total = (int64_t)kr * cnt;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = e / kr, i = e - t * kr;
+    const double wv = w[i0 + t];
+    const double f = use_sqrt ? sqrt(fabs(wv)) : 1.0;
+    C[i + t * ldc] = Q[i + (i0 + t) * ldq] * f;
+    if (yo && i == 0) yo[t] = wv;
+  }
+}
+// normalised residual of Eq. (4.1) from ||H||_F^2, ||W||_F, ||A||_F and ||X||_F^2
+__global__ void resid_kernel(const double* ssH, const double* wF, const double* aF2, const double* ssX,
+                             double* out) {
+  const double num = sqrt(*ssH);
+  const double den = *wF + 2.0 * sqrt(*ssX) * sqrt(*aF2);
+  out[0] = num / den;
+  out[1] = num;
+}
+// ||Z Y Z^T||_F^2 = sum_ij G_ij^2 y_i y_j from G = Z^T Z (y == NULL: Z Z^T)
+__global__ void gram_norm_kernel(const double* __restrict__ G, int c, const double* __restrict__ y, double* out) {
+  double t = 0.0;
+  for (int64_t e = threadIdx.x; e < (int64_t)c * c; e += blockDim.x) {
+    const int64_t j = e / c, i = e - j * c;
+    const double g = G[e];
+    t += g * g * (y ? y[i] * y[j] : 1.0);
+  }
+  __shared__ double sh[32];
+  t = warp_sum(t);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+    *out = fmax(s, 0.0);
+  }
+}
+__global__ void scale_vec_kernel(double* v, int n, double f) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] *= f;
+}
+// Ainv (column-major, ld) [i, perm[c]] = X[i, c] (X row-major)
+template <typename T>
+__global__ void unpermute_kernel(const T* __restrict__ X, const int* __restrict__ perm, int n, double* __restrict__ Ainv,
+                                 int64_t ld) {
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / n, i = e - c * n;
+    Ainv[i + (int64_t)perm[c] * ld] = (double)X[i * n + c];
+  }
+}
+
+static unsigned nblk(int64_t total, int64_t per = 256, int64_t cap = 4096) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(cap, ceil_div(total, per)));
+}
+
+// ---------------------------------------------------------------------------
+// workspace
+// ---------------------------------------------------------------------------
+struct Sizes {
+  int n, m, zcap_w, fcap;
+};
+
+template <typename T>
+static int prepare_newton(Ctx& C, int n, int m, int prec) {
+  const size_t nn = (size_t)n * n;
+  const int zcap = 2 * n + 2 * m + 8;
+  const size_t elt = sizeof(T);
+  LYAP_TRY(ensure(C.gjM0, nn * elt));
+  LYAP_TRY(ensure(C.gjM1, nn * elt));
+  LYAP_TRY(ensure(C.gjPp, (size_t)n * GJ_BS * elt));
+  LYAP_TRY(ensure(C.gjRt, (size_t)n * GJ_BS * elt));
+  LYAP_TRY(ensure(C.gjOrig, (size_t)n * 4));
+  LYAP_TRY(ensure(C.gjPerm0, (size_t)n * 4));
+  LYAP_TRY(ensure(C.gjPerm1, (size_t)n * 4));
+  LYAP_TRY(ensure(C.gjLog, (size_t)n * 8));
+  LYAP_TRY(ensure(C.gjIpiv, (size_t)n * 4));
+  LYAP_TRY(ensure(C.gjStatus, 16));
+  LYAP_TRY(ensure(C.gjExps, (size_t)(2 * ceil_div(n, GJ_BS) + 2) * 4));
+  LYAP_TRY(ensure(C.gjAmax, 64));
+  LYAP_TRY(ensure(C.A0, nn * elt));
+  LYAP_TRY(ensure(C.A1, nn * elt));
+  LYAP_TRY(ensure(C.pinv, (size_t)n * 4));
+  LYAP_TRY(ensure(C.colsum, (size_t)n * 8));
+  LYAP_TRY(ensure(C.Zw, (size_t)n * zcap * elt));
+  LYAP_TRY(ensure(C.Zw2, (size_t)n * zcap * elt));
+  LYAP_TRY(ensure(C.Zh, (size_t)n * zcap * 2 + 256));
+  LYAP_TRY(ensure(C.eZ, (size_t)zcap * 4));
+  LYAP_TRY(ensure(C.yv, (size_t)zcap * 8));
+  LYAP_TRY(ensure(C.yv2, (size_t)zcap * 8));
+  LYAP_TRY(ensure(C.state, sizeof(NewtonState)));
+  LYAP_TRY(ensure(C.scal, 4096));
+  LYAP_TRY(ensure(C.part, (size_t)6 * RED_BLOCKS * 8));
+  LYAP_TRY(ensure(C.dmu, 64 * 8));
+  LYAP_TRY(ensure(C.dex, 64 * 4));
+  // QR scratch (working precision and FP64 share it; size for FP64)
+  LYAP_TRY(ensure(C.qrBar, sizeof(GridBar)));
+  LYAP_TRY(ensure(C.qrStatus, 16));
+  LYAP_TRY(ensure(C.qrCand, 3 * 256 * 8));
+  LYAP_TRY(ensure(C.qrNorms, (size_t)2 * n * 8 + 64));
+  LYAP_TRY(ensure(C.qrPiv, (size_t)n * 4 + 64));
+  LYAP_TRY(ensure(C.qrRdiag, (size_t)zcap * 8 + 64));
+  LYAP_TRY(ensure(C.qrWork, (size_t)n * zcap * 8));
+  LYAP_TRY(ensure(C.qrRank, 16));
+  C.qr.bar = P<GridBar>(C.qrBar);
+  C.qr.status = P<int>(C.qrStatus);
+  C.qr.cand = C.qrCand.p;
+  C.qr.norms = C.qrNorms.p;
+  C.qr.piv = P<int>(C.qrPiv);
+  C.qr.rdiag = C.qrRdiag.p;
+  C.qr.work = C.qrWork.p;
+  C.qr.rank = P<int>(C.qrRank);
+  C.qr.num_sms = C.num_sms;
+  GJWork& W = C.gj;
+  W.n = n;
+  W.elt = (int)elt;
+  W.M[0] = C.gjM0.p;
+  W.M[1] = C.gjM1.p;
+  W.Pp = C.gjPp.p;
+  W.Rt = C.gjRt.p;
+  W.orig = P<int>(C.gjOrig);
+  W.perm[0] = P<int>(C.gjPerm0);
+  W.perm[1] = P<int>(C.gjPerm1);
+  W.logpiv = P<double>(C.gjLog);
+  W.ipiv = nullptr;
+  W.status = P<int>(C.gjStatus);
+  W.exps = P<int>(C.gjExps);
+  W.amax = P<float>(C.gjAmax);
+  (void)prec;
+  return LYAP_OK;
+}
+
+static int prepare_eig(Ctx& C, int q) {
+  const size_t qq = (size_t)q * q;
+  LYAP_TRY(ensure(C.eigWork32, 2 * qq * 4 + 64));
+  LYAP_TRY(ensure(C.eigX, qq * 8 + 64));
+  LYAP_TRY(ensure(C.eigR, qq * 8 + 64));
+  LYAP_TRY(ensure(C.eigS, qq * 8 + 64));
+  LYAP_TRY(ensure(C.eigHX, qq * 8 + 64));
+  LYAP_TRY(ensure(C.eigE, qq * 8 + 64));
+  LYAP_TRY(ensure(C.eigLam, (size_t)q * 8 + 64));
+  LYAP_TRY(ensure(C.eigRed, (size_t)(16 + RED_BLOCKS + 16) * 8));
+  LYAP_TRY(ensure(C.eigW, qq * 8 + 64));
+  LYAP_TRY(ensure(C.eigPv, (size_t)2 * q * 8 + 64));
+  LYAP_TRY(ensure(C.eigInt, (size_t)(3 * q + 16) * 4));
+  C.eig.work32 = P<float>(C.eigWork32);
+  C.eig.X = P<double>(C.eigX);
+  C.eig.R = P<double>(C.eigR);
+  C.eig.S = P<double>(C.eigS);
+  C.eig.HX = P<double>(C.eigHX);
+  C.eig.E = P<double>(C.eigE);
+  C.eig.lam = P<double>(C.eigLam);
+  C.eig.red = P<double>(C.eigRed);
+  C.eig.W = P<double>(C.eigW);
+  C.eig.pv = P<double>(C.eigPv);
+  C.eig.order = P<int>(C.eigInt);
+  C.eig.coff = P<int>(C.eigInt) + q;
+  C.eig.cidx = P<int>(C.eigInt) + 2 * q + 1;
+  C.eig.cinfo = P<int>(C.eigInt) + 3 * q + 4;
+  return LYAP_OK;
+}
+
+static int sync_read(Ctx& C, const void* dev, void* host, size_t bytes) {
+  LYAP_CUDA_TRY(cudaMemcpyAsync(C.hpin, dev, bytes, cudaMemcpyDeviceToHost, C.s));
+  LYAP_CUDA_TRY(cudaStreamSynchronize(C.s));
+  memcpy(host, C.hpin, bytes);
+  return LYAP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the inversion (K1-K3) on the current Newton iterate
+// ---------------------------------------------------------------------------
+template <typename T>
+static int invert_current(Ctx& C, const T* Acur, int n, int prec) {
+  GJWork& W = C.gj;
+  W.cur = 0;
+  LYAP_CUDA_TRY(cudaMemcpyAsync(W.M[0], Acur, sizeof(T) * (size_t)n * n, cudaMemcpyDeviceToDevice, C.s));
+  iota_kernel<<<nblk(n), 256, 0, C.s>>>(W.perm[0], n);
+  LYAP_CUDA_TRY(cudaGetLastError());
+  lyap_count_launch();
+  return gj_invert_run(W, prec, C.s);
+}
+
+// ---------------------------------------------------------------------------
+// one factor step of the Newton iteration, given the stored A_k^{-1} (slot kk)
+// ---------------------------------------------------------------------------
+template <typename T>
+static int factor_product(Ctx& C, int n, int c, int prec, int kk, T* Z) {
+  if (is16(prec)) {
+    const void* Xs = (const char*)C.store.p + (size_t)kk * (size_t)n * C.store_ld * C.store_elt;
+    LYAP_TRY(factor_to_16(prec, (const float*)Z, n, c, n, C.Zh.p, P<int>(C.eZ), C.s));
+    LYAP_TRY(tc_product(prec, n, c, Xs, P<int>(C.dex) + kk, C.Zh.p, P<int>(C.eZ), (float*)Z + (size_t)c * n, n,
+                        C.s));
+  } else {
+    const T* Xs = (const T*)((const char*)C.store.p + (size_t)kk * (size_t)n * C.store_ld * C.store_elt);
+    // Xs is row-major, i.e. the transpose of a column-major n x n matrix
+    LYAP_TRY(gemm<T>('T', 'N', n, c, n, T(1), Xs, n, Z, n, T(0), Z + (size_t)c * n, n, C.s));
+  }
+  return LYAP_OK;
+}
+
+// RankTruncLdlt in working precision T (Sec. 3.2): Z = QR, R Y R^T = V L V^T, keep |l| > tol max|l|.
+template <typename T>
+static int rank_trunc_ldlt(Ctx& C, T* Z, int n, int c, double* y, double tol, int* r_out) {
+  // thin QR of Z (in place in a copy, T precision)
+  T* Fz = (T*)C.qrWork.p;
+  LYAP_TRY((copy_cast<T, T>(Z, n, c, n, Fz, n, 1.0, C.s)));
+  LYAP_TRY(ensure(C.tau, (size_t)(c + 8) * 8));
+  LYAP_TRY(householder_qr<T>(Fz, n, c, n, (T*)C.tau.p, C.qr, C.s));
+  const int kr = std::min(n, c);
+  LYAP_TRY(ensure(C.Tm, (size_t)kr * c * 8 + 64));
+  LYAP_TRY(ensure(C.TP, (size_t)kr * c * 8 + 64));
+  LYAP_TRY(ensure(C.H, (size_t)kr * kr * 8 + 64));
+  LYAP_TRY(ensure(C.w, (size_t)kr * 8 + 64));
+  LYAP_TRY(ensure(C.Qh, (size_t)kr * kr * 8 + 64));
+  LYAP_TRY(ensure(C.Csel, (size_t)kr * kr * 8 + 64));
+  double* R64 = P<double>(C.Tm);
+  // R (kr x c) in FP64
+  {
+    double* tmp = P<double>(C.TP);
+    LYAP_TRY((copy_cast<T, double>(Fz, kr, c, n, tmp, kr, 1.0, C.s)));
+    extract_r_kernel<<<nblk((int64_t)kr * c), 256, 0, C.s>>>(tmp, kr, kr, c, R64);
+    lyap_count_launch();
+  }
+  // M = R diag(y) R^T
+  double* RY = P<double>(C.TP);
+  scale_cols_dev_kernel<<<nblk((int64_t)kr * c), 256, 0, C.s>>>(R64, kr, c, c + 1, y, RY);
+  lyap_count_launch();
+  LYAP_TRY(gemm<double>('N', 'T', kr, kr, c, 1.0, RY, kr, R64, kr, 0.0, P<double>(C.H), kr, C.s));
+  LYAP_TRY(prepare_eig(C, kr));
+  LYAP_TRY(sym_eig(P<double>(C.H), kr, kr, P<double>(C.w), P<double>(C.Qh), kr, sizeof(T) == 8 ? 1 : 0, C.eig, C.s));
+  int* sel = P<int>(C.scal) + 64;
+  select_kernel<<<1, 32, 0, C.s>>>(P<double>(C.w), kr, tol, 1, sel, P<double>(C.scal) + 100);
+  lyap_count_launch();
+  int hs[2];
+  LYAP_TRY(sync_read(C, sel, hs, sizeof(hs)));
+  const int nneg = hs[0], pos = hs[1];
+  const int r = nneg + (kr - pos);
+  // V_t (kr x r) = [Q[:, 0:nneg], Q[:, pos:kr]], y_t = eigenvalues
+  double* Vt = P<double>(C.Csel);
+  double* yt = P<double>(C.yv2);
+  if (nneg > 0) {
+    gather_cols_kernel<<<nblk((int64_t)kr * nneg), 256, 0, C.s>>>(P<double>(C.Qh), kr, kr, P<double>(C.w), 0, nneg, 0,
+                                                                 Vt, kr, yt);
+    lyap_count_launch();
+  }
+  if (kr - pos > 0) {
+    gather_cols_kernel<<<nblk((int64_t)kr * (kr - pos)), 256, 0, C.s>>>(P<double>(C.Qh), kr, kr, P<double>(C.w), pos,
+                                                                       kr - pos, 0, Vt + (size_t)nneg * kr, kr,
+                                                                       yt + nneg);
+    lyap_count_launch();
+  }
+  LYAP_CUDA_TRY(cudaGetLastError());
+  // Z_new = Q [V_t; 0] (working precision)
+  T* Vw = (T*)C.Zw2.p;
+  LYAP_TRY((copy_cast<double, T>(Vt, kr, r, kr, Vw, kr, 1.0, C.s)));
+  LYAP_TRY(apply_q<T>(Fz, n, kr, n, (const T*)C.tau.p, Vw, kr, r, Z, n, C.s));
+  LYAP_CUDA_TRY(cudaMemcpyAsync(y, yt, sizeof(double) * r, cudaMemcpyDeviceToDevice, C.s));
+  *r_out = r;
+  return LYAP_OK;
+}
+
+struct NewtonOpts {
+  int prec, scaling, norm_fro, stop_after, delta_rule, kmax;
+  double tau, scale_off, rank_tol, rho;
+};
+
+// Run the sign-Newton factor iteration on Z (working precision, n x c0 in C.Zw, column-major).
+// compute == true: compute and store the inverse sequence from the working
+// matrix in C.A0 (row-major, already scaled); else replay the stored sequence.
+template <typename T>
+static int newton_run(Ctx& C, int n, int c0, bool ldlt, const NewtonOpts& o, bool compute, int* c_out,
+                      lyap_info_t* info) {
+  NewtonState* st = P<NewtonState>(C.state);
+  const size_t nn = (size_t)n * n;
+  int c = c0;
+  T* Z = P<T>(C.Zw);
+  double* y = P<double>(C.yv);
+  int K = compute ? o.kmax : C.store_count;
+  if (compute) {
+    C.store_count = 0;
+    newton_init_kernel<<<1, 1, 0, C.s>>>(st, o.scaling);
+    lyap_count_launch();
+    LYAP_TRY(sumsq<T>(P<T>(C.A0), n, n, n, &st->ssA, P<double>(C.part), C.s));
+  }
+  T* Acur = P<T>(C.A0);
+  T* Anext = P<T>(C.A1);
+  bool finished = false;
+  for (int kk = 0; kk < K; ++kk) {
+    if (compute) {
+      if (kk >= 64) {
+        lyap_set_error_message("more than 64 Newton steps", __FILE__, __LINE__);
+        return LYAP_ERR_NOCONV;
+      }
+      LYAP_CUDA_TRY(cudaMemsetAsync(C.gj.status, 0, sizeof(int), C.s));
+      LYAP_TRY(invert_current<T>(C, Acur, n, o.prec));
+      const T* X = (const T*)C.gj.M[C.gj.cur];
+      const int* perm = C.gj.perm[C.gj.cur];
+      pinv_kernel<<<nblk(n), 256, 0, C.s>>>(perm, P<int>(C.pinv), n);
+      lyap_count_launch();
+      LYAP_TRY(sumsq<T>(X, n, n, n, &st->ssX, P<double>(C.part), C.s));
+      LYAP_TRY(maxabs<T>(X, n, n, n, &st->maxX, P<double>(C.part), C.s));
+      if (o.scaling == LYAP_SCALE_DET) {
+        sum_vec_kernel<<<1, 32, 0, C.s>>>(C.gj.logpiv, n, &st->logdet);
+        lyap_count_launch();
+      }
+      newton_mu_kernel<<<1, 1, 0, C.s>>>(st, n, o.scaling, is16(o.prec) ? 1 : 0);
+      lyap_count_launch();
+      void* slot = (char*)C.store.p + (size_t)kk * (size_t)n * C.store_ld * C.store_elt;
+      const unsigned nb = RED_BLOCKS;
+      switch (o.prec) {
+        case LYAP_FP64:
+          newton_update_kernel<double, double><<<nb, 256, 0, C.s>>>(n, (const double*)Acur, (const double*)X,
+                                                                    P<int>(C.pinv), st, (double*)Anext,
+                                                                    (double*)slot, C.store_ld, P<double>(C.part));
+          break;
+        case LYAP_FP32:
+          newton_update_kernel<float, float><<<nb, 256, 0, C.s>>>(n, (const float*)Acur, (const float*)X,
+                                                                  P<int>(C.pinv), st, (float*)Anext, (float*)slot, C.store_ld,
+                                                                  P<double>(C.part));
+          break;
+        case LYAP_FP16:
+          newton_update_kernel<float, __half><<<nb, 256, 0, C.s>>>(n, (const float*)Acur, (const float*)X,
+                                                                   P<int>(C.pinv), st, (float*)Anext,
+                                                                   (__half*)slot, C.store_ld, P<double>(C.part));
+          break;
+        case LYAP_BF16:
+          newton_update_kernel<float, __nv_bfloat16><<<nb, 256, 0, C.s>>>(n, (const float*)Acur, (const float*)X,
+                                                                          P<int>(C.pinv), st, (float*)Anext,
+                                                                          (__nv_bfloat16*)slot, C.store_ld, P<double>(C.part));
+          break;
+      }
+      LYAP_CUDA_TRY(cudaGetLastError());
+      newton_sums_kernel<<<1, 96, 0, C.s>>>(P<double>(C.part), nb, st);
+      lyap_count_launch(2);
+      if (!o.norm_fro) {
+        colsum_kernel<T><<<nblk(n, 128), 128, 0, C.s>>>(n, Anext, P<double>(C.colsum));
+        lyap_count_launch();
+        LYAP_TRY(maxabs<double>(P<double>(C.colsum), n, 1, n, &st->stopv, P<double>(C.part) + 3 * RED_BLOCKS, C.s));
+      }
+      newton_test_kernel<<<1, 1, 0, C.s>>>(st, o.tau, o.norm_fro, o.stop_after, o.delta_rule, o.scale_off,
+                                           P<double>(C.dmu), P<int>(C.dex), kk);
+      lyap_count_launch();
+      std::swap(Acur, Anext);
+      C.store_count = kk + 1;
+    }
+    // factor update with the stored A_kk^{-1}
+    if (2 * c + 8 > 2 * n + 8) {
+      lyap_set_error_message("Newton factor exceeds its capacity", __FILE__, __LINE__);
+      return LYAP_ERR_CAPACITY;
+    }
+    LYAP_TRY(factor_product<T>(C, n, c, o.prec, kk, Z));
+    factor_scale_kernel<T><<<ldlt ? 1 : nblk((int64_t)n * 2 * c), 256, 0, C.s>>>(Z, n, n, c, P<double>(C.dmu) + kk,
+                                                                                ldlt ? 1 : 0, y);
+    LYAP_CUDA_TRY(cudaGetLastError());
+    lyap_count_launch();
+    c *= 2;
+    if ((double)c > o.rho * (double)n) {
+      int r = 0;
+      if (!ldlt) {
+        LYAP_TRY(qrcp_truncate<T>(Z, n, c, n, o.rank_tol, C.qr, C.s));
+        LYAP_TRY(sync_read(C, C.qr.rank, &r, sizeof(int)));
+      } else {
+        LYAP_TRY(rank_trunc_ldlt<T>(C, Z, n, c, y, o.rank_tol, &r));
+      }
+      c = r;
+    }
+    if (compute) {
+      NewtonState hst;
+      LYAP_TRY(sync_read(C, st, &hst, sizeof(NewtonState)));
+      int gjs = 0, qrs = 0, tcs = 0;
+      LYAP_TRY(sync_read(C, C.gj.status, &gjs, sizeof(int)));
+      LYAP_TRY(sync_read(C, C.qr.status, &qrs, sizeof(int)));
+      if (is16(o.prec)) {
+        LYAP_TRY(tc_status_read(&tcs));
+        if (tcs) return tcs;
+      }
+      if (info && kk < 64) info->mu[kk] = hst.mu;
+      if (gjs) return gjs;
+      if (qrs) return qrs;
+      if (hst.status) return hst.status;
+      if (hst.done) {
+        finished = true;
+        break;
+      }
+    }
+  }
+  if (compute && !finished) {
+    lyap_set_error_message("sign-Newton reached kmax without meeting its stop test", __FILE__, __LINE__);
+    return LYAP_ERR_NOCONV;
+  }
+  if (!compute) {
+    int qrs = 0;
+    LYAP_TRY(sync_read(C, C.qr.status, &qrs, sizeof(int)));
+    if (qrs) return qrs;
+  }
+  *c_out = c;
+  return LYAP_OK;
+}
+
+}  // namespace lyap
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+using namespace lyap;
+
+extern "C" {
+
+const char* lyap_last_error(void) { return g_err; }
+
+const char* lyap_version(void) { return "liblyap 0.1 (sm_103a)"; }
+
+const char* lyap_status_string(int s) {
+  switch (s) {
+    case LYAP_OK: return "ok";
+    case LYAP_ERR_ARG: return "invalid argument";
+    case LYAP_ERR_NONFINITE: return "non-finite value";
+    case LYAP_ERR_SINGULAR: return "singular pivot";
+    case LYAP_ERR_NOCONV: return "sign-Newton did not converge";
+    case LYAP_ERR_CAPACITY: return "output capacity too small";
+    case LYAP_ERR_TIMEOUT: return "device wait timed out";
+    case LYAP_ERR_CUDA: return "CUDA error";
+    case LYAP_ERR_NOMEM: return "out of device memory";
+    case LYAP_WARN_STAGNATED: return "refinement stagnated";
+    case LYAP_WARN_MAXIT: return "refinement reached imax";
+  }
+  return "unknown status";
+}
+
+int lyap_opts_default(lyap_opts_t* o) {
+  if (!o) return LYAP_ERR_ARG;
+  memset(o, 0, sizeof(*o));
+  o->u_s = LYAP_FP16;
+  o->scaling = LYAP_SCALE_FROB;
+  o->tau_newton = 0.0;
+  o->newton_norm_fro = 0;
+  o->stop_after = 2;
+  o->delta_rule = 1;
+  o->scale_off = 1e-2;
+  o->rank_tol = 0.0;
+  o->rho = 0.1;
+  o->kmax = 50;
+  o->imax = 50;
+  o->tau_ir = 0.0;
+  o->eta_r = 1e-4;
+  o->eta_s = 0.0;
+  o->stag_theta = 0.9;
+  o->stag_count = 2;
+  o->project_psd = 1;
+  return LYAP_OK;
+}
+
+int lyap_ctx_create(lyap_ctx_t** out, void* stream) {
+  if (!out) return LYAP_ERR_ARG;
+  *out = nullptr;
+  int dev = 0;
+  LYAP_CUDA_TRY(cudaGetDevice(&dev));
+  int sms = 0;
+  LYAP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  lyap_ctx* C = new lyap_ctx();
+  C->device = dev;
+  C->s = (cudaStream_t)stream;
+  C->num_sms = sms;
+  if (cudaMallocHost(&C->hpin, 1 << 16) != cudaSuccess) {
+    delete C;
+    lyap_set_error_message("pinned host allocation failed", __FILE__, __LINE__);
+    return LYAP_ERR_NOMEM;
+  }
+  cudaEventCreate(&C->e0);
+  cudaEventCreate(&C->e1);
+  *out = C;
+  return LYAP_OK;
+}
+
+static void free_buf(Buf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+int lyap_ctx_destroy(lyap_ctx_t* C) {
+  if (!C) return LYAP_OK;
+  cudaStreamSynchronize(C->s);
+  Buf* all[] = {&C->state, &C->scal, &C->part, &C->hist, &C->gjM0, &C->gjM1, &C->gjPp, &C->gjRt, &C->gjOrig,
+                &C->gjPerm0, &C->gjPerm1, &C->gjLog, &C->gjIpiv, &C->gjStatus, &C->gjExps, &C->gjAmax, &C->A0,
+                &C->A1, &C->pinv, &C->colsum, &C->Zw, &C->Zw2, &C->Zh, &C->eZ, &C->yv, &C->yv2, &C->store,
+                &C->dmu, &C->dex, &C->F, &C->tau, &C->Tm, &C->TP, &C->H, &C->w, &C->Qh, &C->Csel, &C->Lp,
+                &C->Lm, &C->Zs, &C->Zbest, &C->G, &C->gram, &C->ysol, &C->ybest, &C->ytmp, &C->Lw, &C->Sd,
+                &C->Vs, &C->Lst, &C->qrBar, &C->qrStatus, &C->qrCand, &C->qrNorms, &C->qrPiv, &C->qrRdiag, &C->qrWork,
+                &C->qrRank, &C->eigWork32, &C->eigX, &C->eigR, &C->eigS, &C->eigHX, &C->eigE, &C->eigLam,
+                &C->eigRed, &C->eigW, &C->eigPv, &C->eigInt};
+  for (Buf* b : all) free_buf(*b);
+  if (C->hpin) cudaFreeHost(C->hpin);
+  if (C->e0) cudaEventDestroy(C->e0);
+  if (C->e1) cudaEventDestroy(C->e1);
+  delete C;
+  return LYAP_OK;
+}
+
+int lyap_ctx_set_stream(lyap_ctx_t* C, void* stream) {
+  if (!C) return LYAP_ERR_ARG;
+  C->s = (cudaStream_t)stream;
+  return LYAP_OK;
+}
+
+int lyap_invert(lyap_ctx_t* C, const double* A, int64_t n, int64_t lda, int prec, double* Ainv, int64_t ldai,
+                int32_t* ipiv, double* logabsdet) {
+  if (!C || !A || !Ainv || n <= 0 || lda < n || ldai < n || prec < 0 || prec > 3) return LYAP_ERR_ARG;
+  const int ni = (int)n;
+  if (prec == LYAP_FP64) LYAP_TRY(prepare_newton<double>(*C, ni, 1, prec));
+  else LYAP_TRY(prepare_newton<float>(*C, ni, 1, prec));
+  GJWork& W = C->gj;
+  W.cur = 0;
+  W.ipiv = ipiv;
+  LYAP_CUDA_TRY(cudaMemsetAsync(W.status, 0, sizeof(int), C->s));
+  if (prec == LYAP_FP64) LYAP_TRY(cm64_to_rm<double>(A, n, lda, 1.0, (double*)W.M[0], C->s));
+  else LYAP_TRY(cm64_to_rm<float>(A, n, lda, 1.0, (float*)W.M[0], C->s));
+  iota_kernel<<<nblk(n), 256, 0, C->s>>>(W.perm[0], ni);
+  lyap_count_launch();
+  int st = gj_invert_run(W, prec, C->s);
+  W.ipiv = nullptr;
+  if (st < 0) return st;
+  if (prec == LYAP_FP64)
+    unpermute_kernel<double><<<nblk(n * n), 256, 0, C->s>>>((const double*)W.M[W.cur], W.perm[W.cur], ni, Ainv, ldai);
+  else
+    unpermute_kernel<float><<<nblk(n * n), 256, 0, C->s>>>((const float*)W.M[W.cur], W.perm[W.cur], ni, Ainv, ldai);
+  lyap_count_launch();
+  double* ld = P<double>(C->scal);
+  sum_vec_kernel<<<1, 32, 0, C->s>>>(W.logpiv, ni, ld);
+  lyap_count_launch();
+  LYAP_CUDA_TRY(cudaGetLastError());
+  struct { double ld; } h;
+  LYAP_TRY(sync_read(*C, ld, &h, sizeof(h)));
+  int gs = 0;
+  LYAP_TRY(sync_read(*C, W.status, &gs, sizeof(int)));
+  if (logabsdet) *logabsdet = h.ld;
+  return gs;
+}
+
+int lyap_rank_trunc(lyap_ctx_t* C, double* Z, int64_t n, int64_t c, int64_t ldz, double tol, int64_t* rank_out) {
+  if (!C || !Z || n <= 0 || c < 0 || ldz < n || !rank_out) return LYAP_ERR_ARG;
+  LYAP_TRY(prepare_newton<double>(*C, (int)n, (int)std::max<int64_t>(1, c), LYAP_FP64));
+  LYAP_TRY(ensure(C->qrWork, (size_t)n * c * 8 + 64));
+  C->qr.work = C->qrWork.p;
+  LYAP_TRY(ensure(C->qrRdiag, (size_t)c * 8 + 64));
+  C->qr.rdiag = C->qrRdiag.p;
+  LYAP_CUDA_TRY(cudaMemsetAsync(C->qr.status, 0, sizeof(int), C->s));
+  LYAP_TRY(qrcp_truncate<double>(Z, n, c, ldz, tol, C->qr, C->s));
+  int r = 0, qs = 0;
+  LYAP_TRY(sync_read(*C, C->qr.rank, &r, sizeof(int)));
+  LYAP_TRY(sync_read(*C, C->qr.status, &qs, sizeof(int)));
+  *rank_out = r;
+  return qs;
+}
+
+int lyap_sym_eig(lyap_ctx_t* C, double* H, int64_t q, int64_t ldh, double* w, double* Q, int64_t ldq,
+                 int fp64_refine) {
+  if (!C || !H || !w || !Q || q <= 0 || ldh < q || ldq < q) return LYAP_ERR_ARG;
+  LYAP_TRY(prepare_eig(*C, (int)q));
+  LYAP_TRY(sym_eig(H, q, ldh, w, Q, ldq, fp64_refine, C->eig, C->s));
+  LYAP_CUDA_TRY(cudaStreamSynchronize(C->s));
+  return LYAP_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// solver driver
+// ===========================================================================
+namespace lyap {
+
+struct Problem {
+  const double* A;
+  int n;
+  int64_t lda;
+  const double* L;
+  int64_t ldl;
+  int m;
+  const double* S;
+  int64_t lds;
+};
+
+static NewtonOpts make_newton_opts(const lyap_opts_t& o, int n, bool ldlt) {
+  NewtonOpts no;
+  no.prec = o.u_s;
+  no.scaling = o.scaling;
+  no.norm_fro = o.newton_norm_fro;
+  no.stop_after = o.stop_after;
+  no.delta_rule = o.delta_rule;
+  no.kmax = std::min(o.kmax, 64);
+  const double us = unit_roundoff(o.u_s);
+  no.tau = o.tau_newton > 0 ? o.tau_newton : 10.0 * sqrt((double)n * us);
+  no.scale_off = o.scale_off;
+  no.rank_tol = o.rank_tol > 0 ? o.rank_tol : (ldlt ? us : sqrt(us));
+  no.rho = o.rho;
+  return no;
+}
+
+// Prepare S: diagonalise (S = V diag(s) V^T, L <- L V) so that every inner factor is
+// diagonal.  Returns Lw (n x m FP64, device) and sd (m, device).
+static int prepare_rhs(Ctx& C, const Problem& pb, double** Lw_out, double** sd_out, bool* indefinite) {
+  const int n = pb.n, m = pb.m;
+  LYAP_TRY(ensure(C.Lw, (size_t)n * m * 8 + 64));
+  LYAP_TRY(ensure(C.Sd, (size_t)m * 8 + 64));
+  *indefinite = false;
+  if (!pb.S) {
+    LYAP_TRY((copy_cast<double, double>(pb.L, n, m, pb.ldl, P<double>(C.Lw), n, 1.0, C.s)));
+    *Lw_out = P<double>(C.Lw);
+    *sd_out = nullptr;
+    return LYAP_OK;
+  }
+  LYAP_TRY(ensure(C.Vs, (size_t)m * m * 8 + 64));
+  LYAP_TRY(ensure(C.H, (size_t)m * m * 8 + 64));
+  LYAP_TRY((copy_cast<double, double>(pb.S, m, m, pb.lds, P<double>(C.H), m, 1.0, C.s)));
+  LYAP_TRY(prepare_eig(C, m));
+  LYAP_TRY(sym_eig(P<double>(C.H), m, m, P<double>(C.Sd), P<double>(C.Vs), m, 1, C.eig, C.s));
+  LYAP_TRY(gemm<double>('N', 'N', n, m, m, 1.0, pb.L, pb.ldl, P<double>(C.Vs), m, 0.0, P<double>(C.Lw), n, C.s));
+  std::vector<double> sd(m);
+  LYAP_TRY(sync_read(C, C.Sd.p, sd.data(), sizeof(double) * m));
+  for (double v : sd)
+    if (v < 0) *indefinite = true;
+  *Lw_out = P<double>(C.Lw);
+  *sd_out = P<double>(C.Sd);
+  return LYAP_OK;
+}
+
+// Solve A X + X A^T + Lr diag(yr) Lr^T = 0 with the sign-Newton iteration at u_s;
+// result (FP64, column-major) into Zout (n x r), yout (LDL^T).  Lr is rounded to u_s.
+// compute: build the inverse sequence from A (first solve) or replay it.
+template <typename T>
+static int newton_solve(Ctx& C, const Problem& pb, const double* Lr, int mr, const double* yr, bool ldlt,
+                        const lyap_opts_t& o, bool compute, double* Zout, int64_t ldo, int zcap_out,
+                        double* yout, int* r_out, lyap_info_t* info, int* iters) {
+  const int n = pb.n;
+  NewtonOpts no = make_newton_opts(o, n, ldlt);
+  LYAP_TRY(prepare_newton<T>(C, n, std::max(mr, pb.m), o.u_s));
+  const size_t nn = (size_t)n * n;
+  if (compute) {
+    const size_t selt = (o.u_s == LYAP_FP64) ? 8 : (o.u_s == LYAP_FP32 ? 4 : 2);
+    C.store_ld = (selt == 2) ? ceil_div(n, 8) * 8 : n;  // 16-byte row pitch for the TMA operand
+    LYAP_TRY(ensure(C.store, (size_t)no.kmax * (size_t)n * C.store_ld * selt));
+    C.store_elt = selt;
+    C.store_n = n;
+    C.store_prec = o.u_s;
+    C.store_count = 0;
+    // A_0 = 2^-e0 A (exact power-of-two prescaling: ||A_0||_F in [1, 2))
+    double* sc = P<double>(C.scal);
+    LYAP_TRY(sumsq<double>(pb.A, n, n, pb.lda, sc, P<double>(C.part), C.s));
+    double ssA = 0;
+    LYAP_TRY(sync_read(C, sc, &ssA, sizeof(double)));
+    int e0 = 0;
+    frexp(sqrt(ssA), &e0);
+    e0 -= 1;
+    C.store_e0 = e0;
+    LYAP_TRY(cm64_to_rm<T>(pb.A, n, pb.lda, ldexp(1.0, -e0), P<T>(C.A0), C.s));
+  } else if (C.store_n != n || C.store_prec != o.u_s || C.store_count == 0) {
+    lyap_set_error_message("no stored inverse sequence for this problem", __FILE__, __LINE__);
+    return LYAP_ERR_ARG;
+  }
+  if (mr == 0) {
+    *r_out = 0;
+    if (iters) *iters = C.store_count;
+    return LYAP_OK;
+  }
+  // Z_0 = L rounded to u_s (working precision)
+  {
+    LYAP_TRY(ensure(C.Lst, (size_t)n * mr * 8 + 64));
+    double* tmp = P<double>(C.Lst);
+    LYAP_TRY((copy_cast<double, double>(Lr, n, mr, n, tmp, n, 1.0, C.s)));
+    LYAP_TRY(round_to_prec(tmp, n, mr, n, o.u_s, P<double>(C.part) + 4 * RED_BLOCKS, C.s));
+    LYAP_TRY((copy_cast<double, T>(tmp, n, mr, n, P<T>(C.Zw), n, 1.0, C.s)));
+    if (ldlt) {
+      if (yr) {
+        LYAP_CUDA_TRY(cudaMemcpyAsync(C.yv.p, yr, sizeof(double) * mr, cudaMemcpyDeviceToDevice, C.s));
+      } else {
+        std::vector<double> ones(mr, 1.0);
+        LYAP_CUDA_TRY(cudaMemcpyAsync(C.yv.p, ones.data(), sizeof(double) * mr, cudaMemcpyHostToDevice, C.s));
+        LYAP_CUDA_TRY(cudaStreamSynchronize(C.s));
+      }
+    }
+  }
+  int c = 0;
+  LYAP_TRY(newton_run<T>(C, n, mr, ldlt, no, compute, &c, info));
+  if (iters) *iters = C.store_count;
+  if (c > zcap_out) {
+    *r_out = c;
+    lyap_set_error_message("factor capacity too small", __FILE__, __LINE__);
+    return LYAP_ERR_CAPACITY;
+  }
+  // undo the prescaling: X = 2^-e0 X'  ->  Z = 2^{-e0/2} Z' (Cholesky, with the final 1/sqrt 2),
+  // Y = 2^-e0 Y'/2 (LDL^T)
+  const double e0 = (double)C.store_e0;
+  if (!ldlt) {
+    LYAP_TRY((copy_cast<T, double>(P<T>(C.Zw), n, c, n, Zout, ldo, pow(2.0, -0.5 * e0) / sqrt(2.0), C.s)));
+  } else {
+    LYAP_TRY((copy_cast<T, double>(P<T>(C.Zw), n, c, n, Zout, ldo, 1.0, C.s)));
+    LYAP_CUDA_TRY(cudaMemcpyAsync(yout, C.yv.p, sizeof(double) * c, cudaMemcpyDeviceToDevice, C.s));
+    scale_vec_kernel<<<1, 256, 0, C.s>>>(yout, c, 0.5 * pow(2.0, -e0));
+    lyap_count_launch();
+  }
+  *r_out = c;
+  return LYAP_OK;
+}
+
+static int newton_solve_any(Ctx& C, const Problem& pb, const double* Lr, int mr, const double* yr, bool ldlt,
+                            const lyap_opts_t& o, bool compute, double* Zout, int64_t ldo, int zcap_out,
+                            double* yout, int* r_out, lyap_info_t* info, int* iters) {
+  if (o.u_s == LYAP_FP64)
+    return newton_solve<double>(C, pb, Lr, mr, yr, ldlt, o, compute, Zout, ldo, zcap_out, yout, r_out, info, iters);
+  return newton_solve<float>(C, pb, Lr, mr, yr, ldlt, o, compute, Zout, ldo, zcap_out, yout, r_out, info, iters);
+}
+
+// ---------------------------------------------------------------------------
+// residual factorisation (FP64): Fragment ResFacChol / ResFacLdlt
+// Returns the normalised residual (device scal[40]) and, if want_split, the
+// truncated factors: Cholesky: L+ (n x r+) in C.Lp, L- (n x r-) in C.Lm;
+// LDL^T: L^Delta in C.Lp with values in C.ytmp (r+ = count, r- = 0).
+// ---------------------------------------------------------------------------
+struct ResOut {
+  double res, resF;
+  int rp, rm;
+};
+
+// y == NULL: X = Z Z^T; sd == NULL: W = L L^T.  ldlt selects the split of Fragment ResFacLdlt.
+static int res_fac(Ctx& C, const Problem& pb, const double* Lw, const double* sd, const double* Z, int c,
+                   const double* y, bool ldlt, double eta_r, bool want_split, ResOut* out) {
+  const int n = pb.n, m = pb.m;
+  const int q = 2 * c + m;
+  LYAP_TRY(ensure(C.F, (size_t)n * q * 8 + 64));
+  LYAP_TRY(ensure(C.tau, (size_t)(q + 8) * 8));
+  double* F = P<double>(C.F);
+  // F = [Z, A Z, L]
+  LYAP_TRY((copy_cast<double, double>(Z, n, c, n, F, n, 1.0, C.s)));
+  LYAP_TRY(gemm<double>('N', 'N', n, c, n, 1.0, pb.A, pb.lda, Z, n, 0.0, F + (size_t)c * n, n, C.s));
+  LYAP_TRY((copy_cast<double, double>(Lw, n, m, n, F + (size_t)2 * c * n, n, 1.0, C.s)));
+  LYAP_CUDA_TRY(cudaMemsetAsync(C.qr.status, 0, sizeof(int), C.s));
+  LYAP_TRY(householder_qr<double>(F, n, q, n, P<double>(C.tau), C.qr, C.s));
+  const int kr = std::min(n, q);
+  LYAP_TRY(ensure(C.Tm, (size_t)kr * q * 8 + 64));
+  LYAP_TRY(ensure(C.TP, (size_t)kr * q * 8 + 64));
+  LYAP_TRY(ensure(C.H, (size_t)kr * kr * 8 + 64));
+  extract_r_kernel<<<nblk((int64_t)kr * q), 256, 0, C.s>>>(F, n, kr, q, P<double>(C.Tm));
+  core_right_kernel<<<nblk((int64_t)kr * q), 256, 0, C.s>>>(P<double>(C.Tm), kr, c, m, y, sd, P<double>(C.TP));
+  lyap_count_launch(2);
+  LYAP_TRY(gemm<double>('N', 'T', kr, kr, q, 1.0, P<double>(C.TP), kr, P<double>(C.Tm), kr, 0.0, P<double>(C.H), kr,
+                        C.s));
+  double* sc = P<double>(C.scal);
+  // sc[20] = ||H||_F^2 ; sc[21] = ||X||_F^2 ; sc[22] = ||W||_F ; sc[23] = ||A||_F^2 ; sc[24..25] = res
+  LYAP_TRY(sumsq<double>(P<double>(C.H), kr, kr, kr, sc + 20, P<double>(C.part), C.s));
+  LYAP_TRY(ensure(C.gram, (size_t)std::max(c, m) * std::max(c, m) * 8 + 64));
+  LYAP_TRY(gemm<double>('T', 'N', c, c, n, 1.0, Z, n, Z, n, 0.0, P<double>(C.gram), c, C.s));
+  gram_norm_kernel<<<1, 256, 0, C.s>>>(P<double>(C.gram), c, y, sc + 21);
+  lyap_count_launch();
+  resid_kernel<<<1, 1, 0, C.s>>>(sc + 20, sc + 22, sc + 23, sc + 21, sc + 24);
+  lyap_count_launch();
+  double hres[2];
+  LYAP_TRY(sync_read(C, sc + 24, hres, sizeof(hres)));
+  int qs = 0;
+  LYAP_TRY(sync_read(C, C.qr.status, &qs, sizeof(int)));
+  if (qs) return qs;
+  out->res = hres[0];
+  out->resF = hres[1];
+  out->rp = out->rm = 0;
+  if (!want_split) return LYAP_OK;
+  // eigen-split of H (FP32 accuracy suffices: the split is truncated at eta_r >> u_fp32)
+  LYAP_TRY(ensure(C.w, (size_t)kr * 8 + 64));
+  LYAP_TRY(ensure(C.Qh, (size_t)kr * kr * 8 + 64));
+  LYAP_TRY(ensure(C.Csel, (size_t)kr * kr * 8 + 64));
+  LYAP_TRY(prepare_eig(C, kr));
+  LYAP_TRY(sym_eig(P<double>(C.H), kr, kr, P<double>(C.w), P<double>(C.Qh), kr, 0, C.eig, C.s));
+  int* sel = P<int>(C.scal) + 64;
+  select_kernel<<<1, 32, 0, C.s>>>(P<double>(C.w), kr, eta_r, 0, sel, sc + 30);
+  lyap_count_launch();
+  int hs[2];
+  LYAP_TRY(sync_read(C, sel, hs, sizeof(hs)));
+  const int nneg = hs[0], pos = hs[1];
+  const int npos = kr - pos;
+  double* Cs = P<double>(C.Csel);
+  if (!ldlt) {
+    LYAP_TRY(ensure(C.Lp, (size_t)n * std::max(npos, 1) * 8 + 64));
+    LYAP_TRY(ensure(C.Lm, (size_t)n * std::max(nneg, 1) * 8 + 64));
+    if (npos > 0) {
+      gather_cols_kernel<<<nblk((int64_t)kr * npos), 256, 0, C.s>>>(P<double>(C.Qh), kr, kr, P<double>(C.w), pos, npos,
+                                                                     1, Cs, kr, nullptr);
+      lyap_count_launch();
+      LYAP_TRY(apply_q<double>(F, n, kr, n, P<double>(C.tau), Cs, kr, npos, P<double>(C.Lp), n, C.s));
+    }
+    if (nneg > 0) {
+      gather_cols_kernel<<<nblk((int64_t)kr * nneg), 256, 0, C.s>>>(P<double>(C.Qh), kr, kr, P<double>(C.w), 0, nneg,
+                                                                     1, Cs, kr, nullptr);
+      lyap_count_launch();
+      LYAP_TRY(apply_q<double>(F, n, kr, n, P<double>(C.tau), Cs, kr, nneg, P<double>(C.Lm), n, C.s));
+    }
+    out->rp = npos;
+    out->rm = nneg;
+  } else {
+    const int r = nneg + npos;
+    LYAP_TRY(ensure(C.Lp, (size_t)n * std::max(r, 1) * 8 + 64));
+    LYAP_TRY(ensure(C.Lm, (size_t)(r + 8) * 8));
+    double* yd = P<double>(C.Lm);
+    if (nneg > 0) {
+      gather_cols_kernel<<<nblk((int64_t)kr * nneg), 256, 0, C.s>>>(P<double>(C.Qh), kr, kr, P<double>(C.w), 0, nneg,
+                                                                     0, Cs, kr, yd);
+      lyap_count_launch();
+    }
+    if (npos > 0) {
+      gather_cols_kernel<<<nblk((int64_t)kr * npos), 256, 0, C.s>>>(P<double>(C.Qh), kr, kr, P<double>(C.w), pos, npos,
+                                                                     0, Cs + (size_t)nneg * kr, kr, yd + nneg);
+      lyap_count_launch();
+    }
+    if (r > 0) LYAP_TRY(apply_q<double>(F, n, kr, n, P<double>(C.tau), Cs, kr, r, P<double>(C.Lp), n, C.s));
+    out->rp = r;
+    out->rm = 0;
+  }
+  LYAP_CUDA_TRY(cudaGetLastError());
+  return LYAP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// projected solution update (FP64): Fragment SolUptChol / SolUptLdlt.
+// G = [Z, Z+, Z-] (Cholesky) or [Z, Z^Delta] with weights ups (LDL^T), in C.G.
+// ---------------------------------------------------------------------------
+static int sol_upt(Ctx& C, int n, int qg, int cneg_start, const double* ups, bool psd_keep_positive,
+                   double eta_s, double* Zout, double* yout, int* r_out) {
+  double* G = P<double>(C.G);
+  LYAP_TRY(ensure(C.tau, (size_t)(qg + 8) * 8));
+  LYAP_CUDA_TRY(cudaMemsetAsync(C.qr.status, 0, sizeof(int), C.s));
+  LYAP_TRY(householder_qr<double>(G, n, qg, n, P<double>(C.tau), C.qr, C.s));
+  const int kr = std::min(n, qg);
+  LYAP_TRY(ensure(C.Tm, (size_t)kr * qg * 8 + 64));
+  LYAP_TRY(ensure(C.TP, (size_t)kr * qg * 8 + 64));
+  LYAP_TRY(ensure(C.H, (size_t)kr * kr * 8 + 64));
+  LYAP_TRY(ensure(C.w, (size_t)kr * 8 + 64));
+  LYAP_TRY(ensure(C.Qh, (size_t)kr * kr * 8 + 64));
+  LYAP_TRY(ensure(C.Csel, (size_t)kr * kr * 8 + 64));
+  extract_r_kernel<<<nblk((int64_t)kr * qg), 256, 0, C.s>>>(G, n, kr, qg, P<double>(C.Tm));
+  scale_cols_dev_kernel<<<nblk((int64_t)kr * qg), 256, 0, C.s>>>(P<double>(C.Tm), kr, qg, cneg_start, ups,
+                                                                P<double>(C.TP));
+  lyap_count_launch(2);
+  LYAP_TRY(gemm<double>('N', 'T', kr, kr, qg, 1.0, P<double>(C.TP), kr, P<double>(C.Tm), kr, 0.0, P<double>(C.H), kr,
+                        C.s));
+  LYAP_TRY(prepare_eig(C, kr));
+  LYAP_TRY(sym_eig(P<double>(C.H), kr, kr, P<double>(C.w), P<double>(C.Qh), kr, 1, C.eig, C.s));
+  int* sel = P<int>(C.scal) + 64;
+  select_kernel<<<1, 32, 0, C.s>>>(P<double>(C.w), kr, eta_s, 0, sel, P<double>(C.scal) + 31);
+  lyap_count_launch();
+  int hs[2];
+  LYAP_TRY(sync_read(C, sel, hs, sizeof(hs)));
+  int qs = 0;
+  LYAP_TRY(sync_read(C, C.qr.status, &qs, sizeof(int)));
+  if (qs) return qs;
+  const int nneg = hs[0], pos = hs[1];
+  const int npos = kr - pos;
+  double* Cs = P<double>(C.Csel);
+  int r = 0;
+  if (psd_keep_positive) {
+    if (npos > 0) {
+      gather_cols_kernel<<<nblk((int64_t)kr * npos), 256, 0, C.s>>>(P<double>(C.Qh), kr, kr, P<double>(C.w), pos, npos,
+                                                                     yout ? 0 : 1, Cs, kr, yout);
+      lyap_count_launch();
+    }
+    r = npos;
+  } else {
+    if (nneg > 0) {
+      gather_cols_kernel<<<nblk((int64_t)kr * nneg), 256, 0, C.s>>>(P<double>(C.Qh), kr, kr, P<double>(C.w), 0, nneg,
+                                                                     0, Cs, kr, yout);
+      lyap_count_launch();
+    }
+    if (npos > 0) {
+      gather_cols_kernel<<<nblk((int64_t)kr * npos), 256, 0, C.s>>>(P<double>(C.Qh), kr, kr, P<double>(C.w), pos, npos,
+                                                                     0, Cs + (size_t)nneg * kr, kr,
+                                                                     yout ? yout + nneg : nullptr);
+      lyap_count_launch();
+    }
+    r = nneg + npos;
+  }
+  if (r > 0) LYAP_TRY(apply_q<double>(G, n, kr, n, P<double>(C.tau), Cs, kr, r, Zout, n, C.s));
+  LYAP_CUDA_TRY(cudaGetLastError());
+  *r_out = r;
+  return LYAP_OK;
+}
+
+static int check_problem(const Problem& pb, const lyap_opts_t* o, double* Z, int64_t ldz, int64_t z_cap) {
+  if (!pb.A || !pb.L || !o || !Z) return LYAP_ERR_ARG;
+  if (pb.n <= 0 || pb.m <= 0 || pb.lda < pb.n || pb.ldl < pb.n || ldz < pb.n || z_cap <= 0) return LYAP_ERR_ARG;
+  if (pb.S && pb.lds < pb.m) return LYAP_ERR_ARG;
+  if (o->u_s < 0 || o->u_s > 3 || o->scaling < 0 || o->scaling > 2 || o->kmax <= 0 || o->imax < 0) return LYAP_ERR_ARG;
+  return LYAP_OK;
+}
+
+static int check_inputs_finite(Ctx& C, const Problem& pb) {
+  int* flag = P<int>(C.scal) + 300;
+  LYAP_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), C.s));
+  LYAP_TRY(check_finite(pb.A, pb.n, pb.n, pb.lda, flag, C.s));
+  LYAP_TRY(check_finite(pb.L, pb.n, pb.m, pb.ldl, flag, C.s));
+  if (pb.S) LYAP_TRY(check_finite(pb.S, pb.m, pb.m, pb.lds, flag, C.s));
+  int f = 0;
+  LYAP_TRY(sync_read(C, flag, &f, sizeof(int)));
+  return f ? LYAP_ERR_NONFINITE : LYAP_OK;
+}
+
+static int solve_common(Ctx& C, const Problem& pb, const lyap_opts_t& o, bool refine, double* Z, int64_t ldz,
+                        int64_t z_cap, double* D, int64_t* rank_out, lyap_info_t* info) {
+  const int n = pb.n, m = pb.m;
+  const bool ldlt = (pb.S != nullptr);
+  LYAP_TRY(ensure(C.scal, 4096));
+  LYAP_TRY(ensure(C.part, (size_t)6 * RED_BLOCKS * 8));
+  LYAP_TRY(check_inputs_finite(C, pb));
+  double* Lw = nullptr;
+  double* sd = nullptr;
+  bool indefinite = false;
+  LYAP_TRY(prepare_rhs(C, pb, &Lw, &sd, &indefinite));
+  const int zcap_ir = n + 8;
+  LYAP_TRY(ensure(C.Zs, (size_t)n * (zcap_ir) * 8));
+  LYAP_TRY(ensure(C.Zbest, (size_t)n * (zcap_ir) * 8));
+  LYAP_TRY(ensure(C.ysol, (size_t)(zcap_ir) * 8));
+  LYAP_TRY(ensure(C.ybest, (size_t)(zcap_ir) * 8));
+  // first solve (computes and stores the inverse sequence)
+  int c = 0, iters = 0;
+  LYAP_TRY(newton_solve_any(C, pb, Lw, m, sd, ldlt, o, true, P<double>(C.Zs), n, zcap_ir, P<double>(C.ysol), &c,
+                            info, &iters));
+  info->newton_calls = 1;
+  info->newton_total = iters;
+  info->newton_max = iters;
+  info->n_inversions = iters;
+  // normalisation constants
+  double* sc = P<double>(C.scal);
+  {
+    // ||W||_F from the Gram matrix of L (with the diagonal S), ||A||_F^2
+    LYAP_TRY(ensure(C.gram, (size_t)m * m * 8 + 64));
+    LYAP_TRY(gemm<double>('T', 'N', m, m, n, 1.0, Lw, n, Lw, n, 0.0, P<double>(C.gram), m, C.s));
+    gram_norm_kernel<<<1, 256, 0, C.s>>>(P<double>(C.gram), m, sd, sc + 26);
+    lyap_count_launch();
+    LYAP_TRY(sumsq<double>(pb.A, n, n, pb.lda, sc + 23, P<double>(C.part), C.s));
+    double h[1];
+    LYAP_TRY(sync_read(C, sc + 26, h, sizeof(double)));
+    h[0] = sqrt(h[0]);
+    LYAP_CUDA_TRY(cudaMemcpyAsync(sc + 22, h, sizeof(double), cudaMemcpyHostToDevice, C.s));
+    LYAP_CUDA_TRY(cudaStreamSynchronize(C.s));
+  }
+  const double tau_ir = o.tau_ir > 0 ? o.tau_ir : (double)n * unit_roundoff(LYAP_FP64);
+  const double eta_s = o.eta_s > 0 ? o.eta_s : 10.0 * unit_roundoff(LYAP_FP64);
+  const bool project = (o.project_psd != 0) && !indefinite;
+  double best = 1e300;
+  int best_c = 0;
+  int stag = 0;
+  double res_prev = -1.0;
+  int status = LYAP_OK;
+  info->n_res = 0;
+  const int imax = refine ? o.imax : 0;
+  for (int i = 1; i <= imax + 1; ++i) {
+    ResOut ro;
+    const bool last = (i == imax + 1);
+    LYAP_TRY(res_fac(C, pb, Lw, sd, P<double>(C.Zs), c, ldlt ? P<double>(C.ysol) : nullptr, ldlt, o.eta_r, !last, &ro));
+    if (info->n_res < 64) info->res_hist[info->n_res++] = ro.res;
+    if (ro.res < best) {
+      best = ro.res;
+      best_c = c;
+      LYAP_CUDA_TRY(cudaMemcpyAsync(C.Zbest.p, C.Zs.p, sizeof(double) * (size_t)n * c, cudaMemcpyDeviceToDevice, C.s));
+      if (ldlt) LYAP_CUDA_TRY(cudaMemcpyAsync(C.ybest.p, C.ysol.p, sizeof(double) * c, cudaMemcpyDeviceToDevice, C.s));
+    }
+    if (ro.res <= tau_ir) {
+      info->converged = 1;
+      break;
+    }
+    if (!refine) break;
+    if (res_prev > 0 && ro.res / res_prev > o.stag_theta) ++stag;
+    else stag = 0;
+    res_prev = ro.res;
+    if (stag >= o.stag_count) {
+      info->stagnated = 1;
+      status = LYAP_WARN_STAGNATED;
+      break;
+    }
+    if (last) {
+      status = LYAP_WARN_MAXIT;
+      break;
+    }
+    // correction solves replay the stored inverse sequence (Sec. 3.4)
+    const int rp = ro.rp, rm = ro.rm;
+    const int qg = c + rp + rm;
+    LYAP_TRY(ensure(C.G, (size_t)n * (qg + 4 * n + 16) * 8));
+    double* G = P<double>(C.G);
+    LYAP_TRY((copy_cast<double, double>(P<double>(C.Zs), n, c, n, G, n, 1.0, C.s)));
+    int cp = 0, cm = 0, it2 = 0;
+    if (!ldlt) {
+      // copy L+, L- aside (the Newton solve reuses scratch buffers)
+      LYAP_TRY(ensure(C.Vs, (size_t)n * (rp + rm + 1) * 8 + 64));
+      double* Lpm = P<double>(C.Vs);
+      LYAP_TRY((copy_cast<double, double>(P<double>(C.Lp), n, rp, n, Lpm, n, 1.0, C.s)));
+      LYAP_TRY((copy_cast<double, double>(P<double>(C.Lm), n, rm, n, Lpm + (size_t)n * rp, n, 1.0, C.s)));
+      LYAP_TRY(newton_solve_any(C, pb, Lpm, rp, nullptr, false, o, false, G + (size_t)n * c, n, 2 * n, nullptr, &cp,
+                                nullptr, &it2));
+      LYAP_TRY(newton_solve_any(C, pb, Lpm + (size_t)n * rp, rm, nullptr, false, o, false, G + (size_t)n * (c + cp), n,
+                                2 * n, nullptr, &cm, nullptr, &it2));
+      info->newton_calls += 1;
+      info->newton_total += C.store_count;
+      int rnew = 0;
+      LYAP_TRY(sol_upt(C, n, c + cp + cm, c + cp, nullptr, true, eta_s, P<double>(C.Zs), nullptr, &rnew));
+      c = rnew;
+    } else {
+      LYAP_TRY(ensure(C.Vs, (size_t)n * (rp + 1) * 8 + 64));
+      double* Ld = P<double>(C.Vs);
+      LYAP_TRY((copy_cast<double, double>(P<double>(C.Lp), n, rp, n, Ld, n, 1.0, C.s)));
+      LYAP_TRY(ensure(C.ytmp, (size_t)(2 * n + rp + 16) * 8 * 2 + (size_t)n * rp * 8));
+      // values of S^Delta rounded to u_s
+      double* ups = P<double>(C.ytmp);
+      LYAP_CUDA_TRY(cudaMemcpyAsync(ups, C.ysol.p, sizeof(double) * c, cudaMemcpyDeviceToDevice, C.s));
+      double* sdel = ups + c + 2 * n + 8;
+      LYAP_CUDA_TRY(cudaMemcpyAsync(sdel, C.Lm.p, sizeof(double) * rp, cudaMemcpyDeviceToDevice, C.s));
+      LYAP_TRY(round_to_prec(sdel, rp, 1, rp, o.u_s, P<double>(C.part) + 4 * RED_BLOCKS, C.s));
+      LYAP_TRY(newton_solve_any(C, pb, Ld, rp, sdel, true, o, false, G + (size_t)n * c, n, 2 * n, ups + c, &cp, nullptr,
+                                &it2));
+      info->newton_calls += 1;
+      info->newton_total += C.store_count;
+      int rnew = 0;
+      LYAP_TRY(sol_upt(C, n, c + cp, c + cp, ups, project, eta_s, P<double>(C.Zs), P<double>(C.ysol), &rnew));
+      c = rnew;
+    }
+    info->ir_steps = i;
+    if (c > n) c = n;
+  }
+  // return the best factor
+  if (best_c > z_cap) {
+    *rank_out = best_c;
+    lyap_set_error_message("output capacity too small", __FILE__, __LINE__);
+    return LYAP_ERR_CAPACITY;
+  }
+  LYAP_TRY((copy_cast<double, double>(P<double>(C.Zbest), n, best_c, n, Z, ldz, 1.0, C.s)));
+  if (ldlt && D) LYAP_CUDA_TRY(cudaMemcpyAsync(D, C.ybest.p, sizeof(double) * best_c, cudaMemcpyDeviceToDevice, C.s));
+  LYAP_CUDA_TRY(cudaStreamSynchronize(C.s));
+  *rank_out = best_c;
+  info->rank = best_c;
+  info->res_final = best;
+  return status;
+}
+
+static int solve_entry(lyap_ctx_t* C, const double* A, int64_t n, int64_t lda, const double* L, int64_t ldl, int64_t m,
+                       const double* S, int64_t lds, const lyap_opts_t* opts, double* Z, int64_t ldz, int64_t z_cap,
+                       double* D, int64_t* rank_out, lyap_info_t* info, bool refine) {
+  if (!C || !rank_out) return LYAP_ERR_ARG;
+  Problem pb{A, (int)n, lda, L, ldl, (int)m, S, lds};
+  LYAP_TRY(check_problem(pb, opts, Z, ldz, z_cap));
+  if (S && !D) return LYAP_ERR_ARG;
+  lyap_info_t local;
+  lyap_info_t* inf = info ? info : &local;
+  memset(inf, 0, sizeof(*inf));
+  const int64_t l0 = g_launches;
+  cudaEventRecord(C->e0, C->s);
+  int st = solve_common(*C, pb, *opts, refine, Z, ldz, z_cap, D, rank_out, inf);
+  cudaEventRecord(C->e1, C->s);
+  cudaEventSynchronize(C->e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, C->e0, C->e1);
+  inf->device_ms = ms;
+  inf->kernel_launches = g_launches - l0;
+  inf->status = st;
+  return st;
+}
+
+}  // namespace lyap
+
+extern "C" {
+
+int lyap_sign_solve(lyap_ctx_t* C, const double* A, int64_t n, int64_t lda, const double* L, int64_t ldl, int64_t m,
+                    const double* S, int64_t lds, const lyap_opts_t* opts, double* Z, int64_t ldz, int64_t z_cap,
+                    double* D, int64_t* rank_out, lyap_info_t* info) {
+  return solve_entry(C, A, n, lda, L, ldl, m, S, lds, opts, Z, ldz, z_cap, D, rank_out, info, false);
+}
+
+int lyap_solve_ir(lyap_ctx_t* C, const double* A, int64_t n, int64_t lda, const double* L, int64_t ldl, int64_t m,
+                  const double* S, int64_t lds, const lyap_opts_t* opts, double* Z, int64_t ldz, int64_t z_cap,
+                  double* D, int64_t* rank_out, lyap_info_t* info) {
+  return solve_entry(C, A, n, lda, L, ldl, m, S, lds, opts, Z, ldz, z_cap, D, rank_out, info, true);
+}
+
+int lyap_residual(lyap_ctx_t* C, const double* A, int64_t n, int64_t lda, const double* L, int64_t ldl, int64_t m,
+                  const double* S, int64_t lds, const double* Z, int64_t ldz, int64_t r, const double* D,
+                  double* res_out) {
+  if (!C || !A || !L || !Z || !res_out || n <= 0 || m <= 0 || r < 0 || lda < n || ldl < n || ldz < n) return LYAP_ERR_ARG;
+  Ctx& X = *C;
+  Problem pb{A, (int)n, lda, L, ldl, (int)m, S, lds};
+  LYAP_TRY(ensure(X.scal, 4096));
+  LYAP_TRY(ensure(X.part, (size_t)4 * RED_BLOCKS * 8));
+  LYAP_TRY(prepare_newton<double>(X, (int)n, (int)m, LYAP_FP64));
+  double* Lw = nullptr;
+  double* sd = nullptr;
+  bool indef = false;
+  LYAP_TRY(prepare_rhs(X, pb, &Lw, &sd, &indef));
+  LYAP_TRY(ensure(X.Zs, (size_t)n * std::max<int64_t>(r, 1) * 8));
+  LYAP_TRY((copy_cast<double, double>(Z, n, r, ldz, P<double>(X.Zs), n, 1.0, X.s)));
+  LYAP_TRY(ensure(X.ysol, (size_t)(r + 8) * 8));
+  if (D) LYAP_CUDA_TRY(cudaMemcpyAsync(X.ysol.p, D, sizeof(double) * r, cudaMemcpyDeviceToDevice, X.s));
+  double* sc = P<double>(X.scal);
+  LYAP_TRY(ensure(X.gram, (size_t)m * m * 8 + 64));
+  LYAP_TRY(gemm<double>('T', 'N', m, m, n, 1.0, Lw, n, Lw, n, 0.0, P<double>(X.gram), m, X.s));
+  gram_norm_kernel<<<1, 256, 0, X.s>>>(P<double>(X.gram), (int)m, sd, sc + 26);
+  lyap_count_launch();
+  LYAP_TRY(sumsq<double>(A, n, n, lda, sc + 23, P<double>(X.part), X.s));
+  double h = 0;
+  LYAP_TRY(sync_read(X, sc + 26, &h, sizeof(double)));
+  h = sqrt(h);
+  LYAP_CUDA_TRY(cudaMemcpyAsync(sc + 22, &h, sizeof(double), cudaMemcpyHostToDevice, X.s));
+  LYAP_CUDA_TRY(cudaStreamSynchronize(X.s));
+  ResOut ro;
+  LYAP_TRY(res_fac(X, pb, Lw, sd, P<double>(X.Zs), (int)r, D ? P<double>(X.ysol) : nullptr, D != nullptr, 0.0, false,
+                   &ro));
+  *res_out = ro.res;
+  return LYAP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,28 @@
+// tcgen05 tensor-core GEMMs (sm_103a): TMA-fed 16-bit operands, FP32 accumulators in TMEM.
+#pragma once
+#include "lyap_common.cuh"
+
+namespace lyap {
+
+// Gauss-Jordan trailing update on 16-bit operands (prec = LYAP_FP16 / LYAP_BF16):
+//   Mnew[i, x] = Mcur[orig[i], x] + 2^(eP+eR) sum_t Pp[i, t] Rt[x, t]   for x outside [k, k+bb)
+// Pp, Rt: n x 32 (K-major, 16-bit, scaled by 2^-eP / 2^-eR, exponents in exps[2 step .. 2 step+1]).
+int gj_update_tc(int prec, int n, int k, int bb, int step, const float* Mcur, float* Mnew,
+                 const void* Pp, const void* Rt, const int* orig, const int* exps, cudaStream_t s);
+
+// Factor product on 16-bit operands:
+//   Y[:, j] = 2^(eX + eZ[j]) sum_l Xs[i, l] Zh[j, l]       (i < n, j < c)
+// Xs: n x n row-major 16-bit (K-major A operand), *eX its exponent (device int);
+// Zh: c x n row-major 16-bit (= the n x c factor, column-major; K-major B operand),
+// eZ: per-column exponents (device int[c]); Y: FP32 column-major (ldy).
+int tc_product(int prec, int n, int c, const void* Xs, const int* eX, const void* Zh, const int* eZ,
+               float* Y, int64_t ldy, cudaStream_t s);
+
+// Convert an FP32 column-major factor (n x c, ld) into the 16-bit operand of
+// tc_product with one power-of-two exponent per column.
+// Reads (and clears) the status word of the tensor-core kernels (0 or LYAP_ERR_TIMEOUT).
+int tc_status_read(int* out);
+
+int factor_to_16(int prec, const float* Z, int n, int c, int64_t ld, void* Zh, int* eZ, cudaStream_t s);
+
+}  // namespace lyap

@@ -1,0 +1,281 @@
+"""Thin ctypes binding of the liblyap C ABI (include/liblyap.h).
+
+Argument marshalling only: torch supplies device memory and the current CUDA
+stream, every arithmetic step runs in liblyap's kernels.  Matrices cross the
+boundary column-major FP64 (a torch tensor ``x`` of logical shape (rows, cols) is
+passed through ``_cm(x)``, a column-major copy or view of it).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from . import build_lib
+
+FP64, FP32, FP16, BF16 = 0, 1, 2, 3
+PREC = {"fp64": FP64, "fp32": FP32, "fp16": FP16, "bf16": BF16}
+SCALE_FROB, SCALE_DET, SCALE_NONE = 0, 1, 2
+SCALING = {"frob": SCALE_FROB, "det": SCALE_DET, "none": SCALE_NONE}
+
+OK = 0
+ERR_ARG, ERR_NONFINITE, ERR_SINGULAR, ERR_NOCONV, ERR_CAPACITY, ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM = (
+    -1, -2, -3, -4, -5, -6, -7, -8)
+WARN_STAGNATED, WARN_MAXIT = 1, 2
+
+
+class LyapOpts(C.Structure):
+    _fields_ = [
+        ("u_s", C.c_int), ("scaling", C.c_int), ("tau_newton", C.c_double), ("newton_norm_fro", C.c_int),
+        ("stop_after", C.c_int), ("delta_rule", C.c_int), ("scale_off", C.c_double), ("rank_tol", C.c_double),
+        ("rho", C.c_double), ("kmax", C.c_int), ("imax", C.c_int), ("tau_ir", C.c_double), ("eta_r", C.c_double),
+        ("eta_s", C.c_double), ("stag_theta", C.c_double), ("stag_count", C.c_int), ("project_psd", C.c_int),
+        ("reserved", C.c_int * 8),
+    ]
+
+
+class LyapInfo(C.Structure):
+    _fields_ = [
+        ("status", C.c_int), ("rank", C.c_int), ("ir_steps", C.c_int), ("newton_calls", C.c_int),
+        ("newton_total", C.c_int), ("newton_max", C.c_int), ("n_inversions", C.c_int), ("stagnated", C.c_int),
+        ("converged", C.c_int), ("n_res", C.c_int), ("res_final", C.c_double), ("res_hist", C.c_double * 64),
+        ("mu", C.c_double * 64), ("kernel_launches", C.c_int64), ("device_ms", C.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("res_hist", "mu")}
+        d["res_hist"] = list(self.res_hist[: self.n_res])
+        d["mu"] = [m for m in self.mu[: max(self.newton_max, 0)]]
+        return d
+
+
+class LyapError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"liblyap status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+_P = C.c_void_p
+_I64 = C.c_int64
+_D = C.c_double
+SIGNATURES = {
+    "lyap_opts_default": (C.c_int, [C.POINTER(LyapOpts)]),
+    "lyap_ctx_create": (C.c_int, [C.POINTER(_P), _P]),
+    "lyap_ctx_destroy": (C.c_int, [_P]),
+    "lyap_ctx_set_stream": (C.c_int, [_P, _P]),
+    "lyap_sign_solve": (C.c_int, [_P, _P, _I64, _I64, _P, _I64, _I64, _P, _I64, C.POINTER(LyapOpts), _P, _I64,
+                                  _I64, _P, C.POINTER(_I64), C.POINTER(LyapInfo)]),
+    "lyap_solve_ir": (C.c_int, [_P, _P, _I64, _I64, _P, _I64, _I64, _P, _I64, C.POINTER(LyapOpts), _P, _I64,
+                                _I64, _P, C.POINTER(_I64), C.POINTER(LyapInfo)]),
+    "lyap_residual": (C.c_int, [_P, _P, _I64, _I64, _P, _I64, _I64, _P, _I64, _P, _I64, _I64, _P,
+                                C.POINTER(_D)]),
+    "lyap_invert": (C.c_int, [_P, _P, _I64, _I64, C.c_int, _P, _I64, _P, C.POINTER(_D)]),
+    "lyap_rank_trunc": (C.c_int, [_P, _P, _I64, _I64, _I64, _D, C.POINTER(_I64)]),
+    "lyap_sym_eig": (C.c_int, [_P, _P, _I64, _I64, _P, _P, _I64, C.c_int]),
+    "lyap_last_error": (C.c_char_p, []),
+    "lyap_status_string": (C.c_char_p, [C.c_int]),
+    "lyap_version": (C.c_char_p, []),
+}
+
+
+def lib_path() -> str:
+    return build_lib.LIB_PATH
+
+
+def load(build_if_missing: bool = True):
+    """Load liblyap.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not build_lib.up_to_date():
+        build_lib.build()
+    if not os.path.exists(build_lib.LIB_PATH):
+        raise RuntimeError("liblyap.so is not built; run __graft_entry__.build()")
+    lib = C.CDLL(build_lib.LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, allow_warn: bool = True) -> int:
+    if status < 0 or (status > 0 and not allow_warn):
+        lib = load()
+        raise LyapError(status, f"{lib.lyap_status_string(status).decode()}: {lib.lyap_last_error().decode()}")
+    return status
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _cm(x: torch.Tensor) -> torch.Tensor:
+    """Column-major FP64 CUDA view/copy of a 2-D tensor (ld = rows)."""
+    if x.dtype != torch.float64 or not x.is_cuda:
+        raise TypeError("liblyap takes FP64 CUDA tensors")
+    if x.dim() == 1:
+        x = x[:, None]
+    r, c = x.shape
+    if x.stride() == (1, r) or (c == 1 and x.stride(0) == 1):
+        return x
+    return x.t().contiguous().t()
+
+
+def cm_empty(rows: int, cols: int, device) -> torch.Tensor:
+    return torch.empty((cols, rows), dtype=torch.float64, device=device).t()
+
+
+def cm_copy(x: torch.Tensor) -> torch.Tensor:
+    y = cm_empty(x.shape[0], x.shape[1], x.device)
+    y.copy_(x)
+    return y
+
+
+class Context:
+    """A liblyap context bound to the current torch stream (one per thread)."""
+
+    def __init__(self):
+        lib = load()
+        h = _P()
+        _check(lib.lyap_ctx_create(C.byref(h), _P(_stream())))
+        self.h = h
+        self.lib = lib
+
+    def close(self):
+        if self.h:
+            self.lib.lyap_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _bind(self):
+        self.lib.lyap_ctx_set_stream(self.h, _P(_stream()))
+
+
+_ctx: Context | None = None
+
+
+def context() -> Context:
+    global _ctx
+    if _ctx is None:
+        _ctx = Context()
+    _ctx._bind()
+    return _ctx
+
+
+def make_opts(u_s="fp16", **kw) -> LyapOpts:
+    o = LyapOpts()
+    load().lyap_opts_default(C.byref(o))
+    o.u_s = PREC[u_s] if isinstance(u_s, str) else int(u_s)
+    for k, v in kw.items():
+        if k == "scaling" and isinstance(v, str):
+            v = SCALING[v]
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _solve(fn_name: str, A, L, S=None, z_cap=None, opts: LyapOpts | None = None, raise_on_warn=False):
+    ctx = context()
+    A = _cm(A)
+    L = _cm(L)
+    n, m = L.shape
+    if A.shape != (n, n):
+        raise ValueError("A must be n x n")
+    Sd = _cm(S) if S is not None else None
+    cap = int(z_cap) if z_cap is not None else n
+    Z = cm_empty(n, cap, A.device)
+    D = torch.empty(cap, dtype=torch.float64, device=A.device) if S is not None else None
+    rank = _I64(0)
+    info = LyapInfo()
+    o = opts if opts is not None else make_opts()
+    st = getattr(ctx.lib, fn_name)(ctx.h, _P(A.data_ptr()), n, n, _P(L.data_ptr()), n, m,
+                                   _P(Sd.data_ptr()) if Sd is not None else None, m, C.byref(o),
+                                   _P(Z.data_ptr()), n, cap, _P(D.data_ptr()) if D is not None else None,
+                                   C.byref(rank), C.byref(info))
+    _check(st, allow_warn=not raise_on_warn)
+    r = rank.value
+    return Z[:, :r], (D[:r] if D is not None else None), info
+
+
+def solve_ir(A, L, S=None, z_cap=None, opts=None, **kw):
+    """Mixed-precision IR (Algorithms IR-Chol / IR-LDLT): returns (Z, D, info)."""
+    return _solve("lyap_solve_ir", A, L, S, z_cap, opts if opts is not None else make_opts(**kw))
+
+
+def sign_solve(A, L, S=None, z_cap=None, opts=None, **kw):
+    """One sign-function Newton solve at u_s (Algorithms Newton-Chol / Newton-LDLT)."""
+    return _solve("lyap_sign_solve", A, L, S, z_cap, opts if opts is not None else make_opts(**kw))
+
+
+def residual(A, L, Z, S=None, D=None) -> float:
+    """Relative residual of Eq. (4.1) computed in FP64 on the GPU from the factors."""
+    ctx = context()
+    A, L, Z = _cm(A), _cm(L), _cm(Z)
+    n, m = L.shape
+    r = Z.shape[1]
+    Sd = _cm(S) if S is not None else None
+    Dd = D.contiguous() if D is not None else None
+    out = _D(0.0)
+    _check(ctx.lib.lyap_residual(ctx.h, _P(A.data_ptr()), n, n, _P(L.data_ptr()), n, m,
+                                 _P(Sd.data_ptr()) if Sd is not None else None, m, _P(Z.data_ptr()), n, r,
+                                 _P(Dd.data_ptr()) if Dd is not None else None, C.byref(out)))
+    return out.value
+
+
+def invert(A, prec="fp64"):
+    """Blocked Gauss-Jordan inverse with partial pivoting: returns (Ainv, ipiv, logabsdet)."""
+    ctx = context()
+    A = _cm(A)
+    n = A.shape[0]
+    Ai = cm_empty(n, n, A.device)
+    ipiv = torch.empty(n, dtype=torch.int32, device=A.device)
+    ld = _D(0.0)
+    _check(ctx.lib.lyap_invert(ctx.h, _P(A.data_ptr()), n, n, PREC[prec] if isinstance(prec, str) else prec,
+                               _P(Ai.data_ptr()), n, _P(ipiv.data_ptr()), C.byref(ld)), allow_warn=False)
+    return Ai, ipiv, ld.value
+
+
+def rank_trunc(Z, tol: float):
+    """RankTruncChol: QR with column pivoting of Z^T; returns Pi [T C]^T (n x r)."""
+    ctx = context()
+    Zc = cm_copy(Z)
+    n, c = Zc.shape
+    r = _I64(0)
+    _check(ctx.lib.lyap_rank_trunc(ctx.h, _P(Zc.data_ptr()), n, c, n, float(tol), C.byref(r)), allow_warn=False)
+    return Zc[:, : r.value]
+
+
+def sym_eig(H, refine: bool = True):
+    """Symmetric eigendecomposition H = Q diag(w) Q^T (ascending w)."""
+    ctx = context()
+    Hc = cm_copy(H)
+    q = Hc.shape[0]
+    w = torch.empty(q, dtype=torch.float64, device=H.device)
+    Q = cm_empty(q, q, H.device)
+    _check(ctx.lib.lyap_sym_eig(ctx.h, _P(Hc.data_ptr()), q, q, _P(w.data_ptr()), _P(Q.data_ptr()), q,
+                                1 if refine else 0), allow_warn=False)
+    return w, Q
+
+
+def exported_symbols() -> list[str]:
+    return list(SIGNATURES)
+
+
+# The C entry points under their own names (same arguments as the wrappers above).
+lyap_solve_ir = solve_ir
+lyap_sign_solve = sign_solve
+lyap_residual = residual
+lyap_invert = invert
+lyap_rank_trunc = rank_trunc
+lyap_sym_eig = sym_eig

@@ -1,0 +1,122 @@
+"""Kernel-level parity of the CUDA path (through the C ABI) against the CPU oracle
+and against the mathematics of each kernel: inversion (K1-K3), QR with column
+pivoting (K6), symmetric eigendecomposition (K9), residual verifier (K13)."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import lyapgen as gen
+import oracle as O
+from tests.gpu_util import N, T, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def lib():
+    from paper_2510_02126_gb300 import lyap
+    return lyap
+
+
+@pytest.mark.parametrize("n", [1, 2, 17, 31, 32, 33, 64, 100, 257, 1024])
+def test_invert_fp64_matches_lapack_and_pivots(n):
+    g = gen.rng(1000 + n)
+    A = g.standard_normal((n, n))
+    Ai, ipiv, logdet = lib().invert(T(A), "fp64")
+    Ai = N(Ai)
+    ref = np.linalg.inv(A)
+    assert rel(Ai, ref) < 1e-10 * max(1.0, np.linalg.cond(A) / 1e3)
+    # the pivot sequence is the getrf one (largest |a_ij|, lowest row on ties)
+    _, _, piv = O.getrf_pp(A)
+    assert np.array_equal(N(ipiv).astype(np.int64), piv)
+    assert abs(logdet - np.linalg.slogdet(A)[1]) < 1e-9 * max(1.0, abs(logdet))
+
+
+@pytest.mark.parametrize("prec,u", [("fp32", 2.0 ** -24), ("fp16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
+@pytest.mark.parametrize("n", [7, 64, 130, 512, 1024])
+def test_invert_low_precision_error_bound(prec, u, n):
+    g = gen.rng(2000 + n)
+    A = g.standard_normal((n, n)) + 2 * n ** 0.5 * np.eye(n)  # moderately conditioned
+    Ai = N(lib().invert(T(A), prec)[0])
+    kappa = np.linalg.cond(A)
+    err = np.linalg.norm(A @ Ai - np.eye(n)) / np.sqrt(n)
+    assert err <= 10 * n ** 0.5 * u * kappa, (err, kappa)
+
+
+def test_invert_bf16_and_fp16_use_distinct_rounding():
+    g = gen.rng(77)
+    A = g.standard_normal((256, 256)) + 16 * np.eye(256)
+    e16 = np.linalg.norm(A @ N(lib().invert(T(A), "fp16")[0]) - np.eye(256))
+    eb = np.linalg.norm(A @ N(lib().invert(T(A), "bf16")[0]) - np.eye(256))
+    e32 = np.linalg.norm(A @ N(lib().invert(T(A), "fp32")[0]) - np.eye(256))
+    assert e32 < e16 < eb
+
+
+def test_invert_singular_reports_error():
+    A = np.ones((8, 8))
+    with pytest.raises(Exception) as ei:
+        lib().invert(T(A), "fp64")
+    assert getattr(ei.value, "status", None) == lib().ERR_SINGULAR
+
+
+def test_invert_nonfinite_reports_error():
+    A = np.eye(8)
+    A[3, 3] = np.nan
+    with pytest.raises(Exception) as ei:
+        lib().invert(T(A), "fp64")
+    assert getattr(ei.value, "status", None) in (lib().ERR_NONFINITE, lib().ERR_SINGULAR)
+
+
+@pytest.mark.parametrize("n,r,c", [(80, 7, 30), (1024, 40, 200), (64, 1, 3), (33, 33, 33)])
+def test_rank_trunc_exact_rank(n, r, c):
+    g = gen.rng(n + r + c)
+    Z = g.standard_normal((n, r)) @ g.standard_normal((r, c))
+    Zt = N(lib().rank_trunc(T(Z), 1e-10))
+    assert Zt.shape[1] == min(r, c)
+    assert rel(Zt @ Zt.T, Z @ Z.T) < 1e-11
+
+
+def test_rank_trunc_matches_oracle_rank_and_bound():
+    g = gen.rng(5)
+    n, c = 300, 60
+    U, _ = np.linalg.qr(g.standard_normal((n, c)))
+    Z = (U * 10.0 ** -np.linspace(0, 14, c)) @ np.linalg.qr(g.standard_normal((c, c)))[0]
+    for tol in (1e-4, 1e-8, 1e-12):
+        Zt = N(lib().rank_trunc(T(Z), tol))
+        Zo = O.rank_trunc_chol(Z, tol)
+        assert abs(Zt.shape[1] - Zo.shape[1]) <= 1
+        err = np.linalg.norm(Z @ Z.T - Zt @ Zt.T, 2)
+        # truncation bound of RankTruncChol plus the FP64 rounding of the products
+        assert err <= 1.01 * (tol * np.linalg.norm(Z, 2)) ** 2 + 50 * n * 2.0 ** -53 * np.linalg.norm(Z, 2) ** 2
+
+
+@pytest.mark.parametrize("q", [1, 2, 5, 64, 129, 160, 161, 300])
+@pytest.mark.parametrize("refine", [False, True])
+def test_sym_eig(q, refine):
+    g = gen.rng(300 + q)
+    B = g.standard_normal((q, q))
+    H = (B + B.T) / 2
+    H[0, 0] += 3.0
+    w, Q = lib().sym_eig(T(H), refine)
+    w, Q = N(w), N(Q)
+    wref = np.linalg.eigvalsh(H)
+    tol = 1e-12 if refine else 2e-5
+    nh = np.linalg.norm(H, 2)
+    assert np.max(np.abs(w - wref)) <= tol * nh * max(1, q ** 0.5)
+    assert np.linalg.norm(H @ Q - Q * w) <= tol * nh * q
+    assert np.linalg.norm(Q.T @ Q - np.eye(q)) <= tol * q
+    assert np.all(np.diff(w) >= -tol * nh)
+
+
+def test_residual_verifier_matches_explicit():
+    d = gen.convdiff_shifted(grid=10, m=3)
+    A, L = d["A"], d["L"]
+    g = gen.rng(9)
+    Z = g.standard_normal((100, 12))
+    res = lib().residual(T(A), T(L), T(Z))
+    ref = O.residual_eq41(A, Z, L @ L.T)
+    assert abs(res - ref) <= 1e-12 * ref
+    S = np.diag([1.0, -1.0, 2.0])
+    y = g.standard_normal(12)
+    res = lib().residual(T(A), T(L), T(Z), S=T(S), D=T(y))
+    ref = O.residual_eq41(A, Z, L @ S @ L.T, y)
+    assert abs(res - ref) <= 1e-12 * ref

@@ -1,0 +1,156 @@
+"""Solver-level parity of the CUDA path (C ABI) with the CPU oracle: the
+sign-Newton solver (Algorithms Newton-Chol / Newton-LDLT) and the mixed-precision
+IR algorithms, judged on the exact solution (Schur method), the relative residual
+of Eq. (4.1), and the iteration counts that depend on A only."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import lyapgen as gen
+import oracle as O
+from tests.gpu_util import N, T, rel
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def lib():
+    from paper_2510_02126_gb300 import lyap
+    return lyap
+
+
+FP64_LAPLACE = dict(u_s="fp64", scaling="det", newton_norm_fro=1, rho=0.0, rank_tol=1e-14)
+
+
+@pytest.mark.parametrize("grid", [4, 8])
+def test_sign_solve_fp64_laplacian(grid):
+    d = gen.fp64_laplacian(grid, 2)
+    A, L = d["A"], d["L"]
+    n = A.shape[0]
+    W = L @ L.T
+    X = O.bartels_stewart(A, W)
+    Z, _, info = lib().sign_solve(T(A), T(L), tau_newton=1e-12 * n, **FP64_LAPLACE)
+    Z = N(Z)
+    opts = O.Opts(u_s="fp64", scaling="det", newton_norm="fro", tau_newton=1e-12 * n, rho=0.0, rank_tol=1e-14)
+    Zo, rec = O.newton_chol(A, L, opts)
+    assert info.newton_max == len(rec.inverses)
+    assert np.allclose(list(info.mu)[1:info.newton_max], rec.mus[1:], rtol=1e-9)
+    assert rel(Z @ Z.T, X) <= 1e-10
+    assert O.residual_eq41(A, Z, W) <= 1e-12
+    assert abs(Z.shape[1] - Zo.shape[1]) <= 2
+
+
+def test_table41_fp64_counts_on_gpu():
+    gold = json.load(open(os.path.join(HERE, "golden", "table41_fp64_newton_counts.json")))
+    for q, alpha in zip(gold["q"], gold["alpha"]["100"]["chol"]):
+        d = gen.paper_synthetic(100, q)
+        Z, _, info = lib().sign_solve(T(d["A"]), T(d["L"]), u_s="fp64")
+        assert info.newton_max == alpha, (q, info.newton_max, alpha)
+        X = O.bartels_stewart(d["A"], d["L"] @ d["L"].T)
+        assert rel(N(Z) @ N(Z).T, X) <= 1e-10
+
+
+@pytest.mark.parametrize("u_s,kappa", [("fp64", 1e3), ("fp32", 1e3), ("fp16", 1e2), ("fp16", 1e3), ("bf16", 1e2)])
+def test_ir_chol_convdiff(u_s, kappa):
+    d = gen.convdiff_shifted(grid=12, m=3, kappa=kappa)
+    A, L = d["A"], d["L"]
+    W = L @ L.T
+    X = O.bartels_stewart(A, W)
+    Z, _, info = lib().solve_ir(T(A), T(L), u_s=u_s, tau_ir=1e-12)
+    Z = N(Z)
+    assert info.converged, info.as_dict()
+    assert O.residual_eq41(A, Z, W) <= 1e-12
+    assert rel(Z @ Z.T, X) <= 1e-10
+    assert abs(info.res_final - O.residual_eq41(A, Z, W)) <= 1e-3 * info.res_final + 1e-16
+    # the inverse sequence is computed once and replayed by every correction solve
+    assert info.n_inversions == info.newton_max
+    assert info.newton_total == info.newton_calls * info.newton_max
+
+
+@pytest.mark.parametrize("u_s,p", [("fp64", 1), ("fp32", 2), ("fp16", 1), ("bf16", 1)])
+def test_ir_ldlt_indefinite(u_s, p):
+    d = gen.normal_blocks(n=128, p=p, m=4)
+    A, L, S = d["A"], d["L"], d["S"]
+    W = L @ S @ L.T
+    X = O.bartels_stewart(A, W)
+    Z, D, info = lib().solve_ir(T(A), T(L), S=T(S), u_s=u_s, tau_ir=1e-12)
+    Z, D = N(Z), N(D)
+    assert info.converged, info.as_dict()
+    assert O.residual_eq41(A, Z, W, D) <= 1e-12
+    assert rel((Z * D) @ Z.T, X) <= 1e-10
+
+
+def test_ir_ldlt_psd_matches_chol():
+    d = gen.paper_synthetic(80, 1.5)
+    A, L = d["A"], d["L"]
+    X = O.bartels_stewart(A, L @ L.T)
+    Z, D, info = lib().solve_ir(T(A), T(L), S=T(np.eye(3)), u_s="fp16", tau_ir=1e-12)
+    assert info.converged
+    assert np.all(N(D) > 0)
+    assert rel((N(Z) * N(D)) @ N(Z).T, X) <= 1e-10
+
+
+def test_ir_config_convdiff_1024_fp16():
+    d = gen.convdiff_shifted()
+    A, L = d["A"], d["L"]
+    W = L @ L.T
+    Z, _, info = lib().solve_ir(T(A), T(L), u_s="fp16", tau_ir=1e-12, imax=50)
+    Z = N(Z)
+    res = O.residual_eq41(A, Z, W)
+    assert info.converged and res <= 1e-12, (res, info.as_dict())
+    X = O.bartels_stewart(A, W)
+    assert rel(Z @ Z.T, X) <= 1e-10
+
+
+def test_fp64_sign_newton_config_convdiff_1024():
+    d = gen.convdiff_shifted()
+    A, L = d["A"], d["L"]
+    W = L @ L.T
+    Z, _, info = lib().sign_solve(T(A), T(L), u_s="fp64")
+    rec = O.newton_sequence(A, O.Opts(u_s="fp64"))
+    assert info.newton_max == len(rec.inverses)
+    assert O.residual_eq41(A, N(Z), W) <= 1e-12
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_scalar_equation():
+    A = np.array([[-2.0]])
+    L = np.array([[3.0]])
+    Z, _, info = lib().solve_ir(T(A), T(L), u_s="fp16", tau_ir=1e-14)
+    assert abs(N(Z)[0, 0] ** 2 - 9.0 / 4.0) <= 1e-13
+
+
+def test_single_rhs_column_fp32():
+    d = gen.convdiff_shifted(grid=7, m=1)
+    A, L = d["A"], d["L"]
+    X = O.bartels_stewart(A, L @ L.T)
+    Z, _, info = lib().solve_ir(T(A), T(L), u_s="fp32", tau_ir=1e-12)
+    assert rel(N(Z) @ N(Z).T, X) <= 1e-10
+
+
+def test_capacity_error():
+    d = gen.convdiff_shifted(grid=6, m=2)
+    with pytest.raises(Exception) as ei:
+        lib().solve_ir(T(d["A"]), T(d["L"]), u_s="fp64", z_cap=2)
+    assert getattr(ei.value, "status", None) == lib().ERR_CAPACITY
+
+
+def test_nonfinite_input():
+    d = gen.convdiff_shifted(grid=5, m=2)
+    A = d["A"].copy()
+    A[1, 2] = np.inf
+    with pytest.raises(Exception) as ei:
+        lib().solve_ir(T(A), T(d["L"]), u_s="fp16")
+    assert getattr(ei.value, "status", None) == lib().ERR_NONFINITE
+
+
+def test_non_hurwitz_does_not_converge():
+    # eigenvalues +-i on the imaginary axis: the sign function is undefined
+    A = np.kron(np.eye(4), np.array([[0.0, 1.0], [-1.0, 0.0]]))
+    L = np.ones((8, 1))
+    with pytest.raises(Exception) as ei:
+        lib().sign_solve(T(A), T(L), u_s="fp64", kmax=30)
+    assert getattr(ei.value, "status", None) in (lib().ERR_NOCONV, lib().ERR_NONFINITE, lib().ERR_SINGULAR)
