@@ -1,0 +1,309 @@
+#!/usr/bin/env python
+"""Benchmark: Lyapunov solves/s at relative residual <= 1e-12, mixed-precision IR
+(FP16 inner sign-Newton, FP64 refinement) against the plain FP64 sign-Newton solver,
+both on the GPU through liblyap's C ABI.
+
+Workload (one step = one complete solve): A = -(32 x 32 upwind convection-diffusion,
+velocity (10, 10), h = 1/33) + sigma I with sigma chosen so that the eigenvalue ratio of
+the Lyapunov operator is 1e3; W = L L^T with L 1024 x 4 N(0, 1).  Synthetic, seeded.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank solves its own copy (independent problems, no collective on
+the data path); rank 0 prints one JSON line.  ``--impl reference`` times the CPU oracle
+(test infrastructure, plain numpy/scipy) on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Lyapunov solves/s at norm. residual ≤1e-12: mixed-prec IR vs FP64 sign-Newton"
+UNIT = "solves/s"
+TAU = 1e-12
+WORKLOAD = ("convdiff 32x32 upwind (10,10) shifted to kappa~1e3, n=1024, W=LL^T m=4; "
+            "FP16 inner sign-Newton (FP32 accumulate), FP64 refinement to 1e-12, imax=10")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_problem():
+    import lyapgen
+    return lyapgen.convdiff_shifted(grid=32, m=4, vel=10.0, kappa=1e3)
+
+
+def cpu_oracle_solve(A, L):
+    import oracle as O
+    t0 = time.perf_counter()
+    Z, info = O.ir_chol(A, L, O.Opts(u_s="fp16", tau_ir=TAU))
+    dt = time.perf_counter() - t0
+    return dt, O.residual_eq41(A, Z, L @ L.T), info
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    d = make_problem()
+    A, L = d["A"], d["L"]
+    times, ress = [], []
+    for i in range(args.warmup + args.steps):
+        dt, res, info = cpu_oracle_solve(A, L)
+        if i >= args.warmup:
+            times.append(dt)
+            ress.append(res)
+    ms = 1000.0 * sum(times) / len(times)
+    ok = all(r <= TAU for r in ress)
+    value = (1000.0 / ms) if ok else 0.0
+    cores = host_cores()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 (fp16 rounding emulated)", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": 1024, "m": 4, "u_s": "fp16", "tau_ir": TAU},
+        "res_final_max": max(ress),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "one complete oracle IR solve (numpy/scipy FP64 with FP16 rounding emulation) "
+                                   "of the benchmark workload per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2510_02126_gb300 import lyap
+
+    # CPU baseline first (oracle, rank 0, N = 1), before any timing on the GPU
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        d = make_problem()
+        dt, res, info = cpu_oracle_solve(d["A"], d["L"])
+        cpu = {"value": (1.0 / dt) if res <= TAU else 0.0, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+               "sample": f"one complete oracle IR solve of the benchmark workload ({dt:.1f} s, residual {res:.1e}, "
+                         f"{info.ir_steps} refinement steps; FP16 rounding emulated in numpy)"}
+
+    d = make_problem()
+    A_np, L_np = d["A"], d["L"]
+    n, m = L_np.shape
+    A = torch.tensor(A_np, device=dev)
+    L = torch.tensor(L_np, device=dev)
+    opts_ir = lyap.make_opts("fp16", tau_ir=TAU, imax=10, profile=1)
+    opts_64 = lyap.make_opts("fp64", tau_ir=TAU, profile=1)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            fn()
+        barrier()
+        tot, infos = 0.0, []
+        for _ in range(steps):
+            flush.fill_(1.0)  # evict L2 between timed steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+            infos.append(out)
+        barrier()
+        ms = tot / steps
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, infos
+
+    def solve_ir():
+        Z, _, info = lyap.solve_ir(A, L, opts=opts_ir)
+        return info
+
+    def solve_64():
+        Z, _, info = lyap.sign_solve(A, L, opts=opts_64)
+        return info
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms_ir, infos_ir = timed(solve_ir, args.steps, args.warmup)
+    clocks = sampler.stop()
+    ms_64, infos_64 = timed(solve_64, max(1, min(args.steps, 3)), min(args.warmup, 3))
+
+    res_ir = max(i.res_final for i in infos_ir)
+    res_64 = max(i.res_final for i in infos_64)
+    ok_ir = all(i.converged for i in infos_ir) and res_ir <= TAU
+    value = (world * 1000.0 / ms_ir) if ok_ir else 0.0
+    v64 = (world * 1000.0 / ms_64) if res_64 <= TAU else 0.0
+
+    # end to end: pinned host inputs -> device -> solve -> factor back to the host
+    A_h = torch.tensor(A_np).pin_memory()
+    L_h = torch.tensor(L_np).pin_memory()
+
+    def e2e_step():
+        Ad = A_h.to(dev, non_blocking=True)
+        Ld = L_h.to(dev, non_blocking=True)
+        Z, _, info = lyap.solve_ir(Ad, Ld, opts=opts_ir)
+        Zh = Z.to("cpu")
+        e2e_step.out_bytes = Zh.numel() * 8
+        return info
+
+    e2e_step.out_bytes = 0
+    ms_e2e, infos_e2e = timed(e2e_step, max(1, min(args.steps, 3)), 1)
+    ok_e2e = all(i.converged for i in infos_e2e)
+
+    # roofline of the dominant phase, from CUDA events recorded by the library on this stream
+    pk, pk_kind = peaks()
+    phase = {k: 0.0 for k in lyap.PHASES}
+    calls = {k: 0 for k in lyap.PHASES}
+    for i in infos_ir:
+        dd = i.as_dict()
+        for k in lyap.PHASES:
+            phase[k] += dd["phase_ms"][k] / len(infos_ir)
+            calls[k] += dd["phase_calls"][k] / len(infos_ir)
+    dom = max(phase, key=phase.get)
+    n_inv = infos_ir[0].n_inversions
+    inv_ms = phase["invert"] / max(1, n_inv)
+    inv_tflops = 2.0 * n ** 3 / (inv_ms * 1e-3) / 1e12 if inv_ms > 0 else 0.0
+    peak_tc = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+    roofline = {"kernel": "gj_invert (panel + tcgen05 trailing update), one n x n inversion",
+                "bound": "tensor", "achieved": inv_tflops, "peak": peak_tc, "unit": "TFLOP/s",
+                "frac": inv_tflops / peak_tc, "traffic": None,
+                "work": f"2 n^3 = {2 * n ** 3:.3e} flop per inversion; {n_inv} inversions per solve",
+                "peak_kind": f"{pk_kind} bf16 sustained (FP16 has the same nominal dense rate)",
+                "dominant_phase": dom, "phase_ms_per_solve": phase, "phase_calls_per_solve": calls}
+
+    launches = int(sum(i.kernel_launches for i in infos_ir))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_ir, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f16 (inner, FP32 accumulate) + f64 (refinement)", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "m": m, "u_s": "fp16", "tau_ir": TAU, "imax": 10,
+                   "l2": "flushed between timed steps (256 MiB write)"},
+        "res_final_max": res_ir, "ir_steps": [i.ir_steps for i in infos_ir],
+        "newton_inversions": n_inv, "rank": [i.rank for i in infos_ir],
+        "fp64_sign_newton": {"value": v64, "unit": UNIT, "ms_per_solve": ms_64, "res_final_max": res_64,
+                             "inversions": infos_64[0].n_inversions},
+        "speedup_vs_fp64_sign_newton": (value / v64) if v64 > 0 else None,
+        "e2e": {"value": (world * 1000.0 / ms_e2e) if ok_e2e else 0.0, "unit": UNIT,
+                "h2d_bytes_per_step": int(A_np.nbytes + L_np.nbytes), "d2h_bytes_per_step": int(e2e_step.out_bytes)},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -79,8 +79,21 @@ typedef struct {
   double stag_theta;    /* stagnation ratio (0.9) */
   int stag_count;       /* consecutive stagnating steps that stop IR (2) */
   int project_psd;      /* 1: PSD projection in the solution update (forced off for indefinite S) */
-  int reserved[8];
+  int profile;          /* 1: record per-phase device times into lyap_info_t.phase_ms (CUDA events) */
+  int reserved[7];
 } lyap_opts_t;
+
+/* Phases reported in lyap_info_t.phase_ms / phase_calls when opts.profile = 1. */
+enum {
+  LYAP_PHASE_INVERT = 0,   /* n x n inversions (panel + trailing-update kernels) */
+  LYAP_PHASE_NEWTON = 1,   /* Newton scalar/epilogue kernels (scaling, A_{k+1}, stop test) */
+  LYAP_PHASE_FACTOR = 2,   /* factor products A_k^{-1} Z_k and their scaling */
+  LYAP_PHASE_COMPRESS = 3, /* rank truncation inside the Newton iteration */
+  LYAP_PHASE_RESFAC = 4,   /* residual factorisation without its eigensolver (A Z, QR, core matrix) */
+  LYAP_PHASE_EIG = 5,      /* symmetric eigensolvers */
+  LYAP_PHASE_SOLUPT = 6,   /* projected solution update without its eigensolver */
+  LYAP_PHASE_OTHER = 7
+};
 
 typedef struct {
   int status;           /* same value as returned */
@@ -98,6 +111,8 @@ typedef struct {
   double mu[64];        /* Newton scaling parameters mu_0, mu_1, ... */
   int64_t kernel_launches; /* CUDA kernels launched by this call */
   double device_ms;     /* device time of the call (CUDA events on the context stream) */
+  double phase_ms[8];   /* per-phase device time (opts.profile = 1), LYAP_PHASE_* */
+  int64_t phase_calls[8];
 } lyap_info_t;
 
 /* Fill *o with the paper's defaults (u_s = FP16).  Returns LYAP_OK. */

@@ -7,26 +7,30 @@ namespace lyap {
 // Thread (tx, ty) owns rows tx + 16 a and columns ty + 16 b, so that every store
 // of a half warp covers 16 consecutive rows of the column-major C.
 // ---------------------------------------------------------------------------
-template <typename T, bool TA, bool TB>
+// TILE x TILE output tile (TILE = 64 or 32), 16-deep K slices, 256 threads, each owning
+// (TILE/16) x (TILE/16) outputs.
+template <typename T, bool TA, bool TB, int TILE>
 __global__ void __launch_bounds__(256)
 gemm_kernel(int64_t M, int64_t N, int64_t K, T alpha, const T* __restrict__ A, int64_t lda,
             const T* __restrict__ B, int64_t ldb, T beta, T* __restrict__ C, int64_t ldc) {
-  __shared__ T As[16][64 + 1];
-  __shared__ T Bs[16][64 + 1];
+  constexpr int RA = TILE / 16;            // outputs per thread along each dimension
+  constexpr int LD = TILE * 16 / 256;      // loads per thread per operand slice
+  __shared__ T As[16][TILE + 1];
+  __shared__ T Bs[16][TILE + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int64_t m0 = (int64_t)blockIdx.x * 64, n0 = (int64_t)blockIdx.y * 64;
-  T acc[4][4];
+  const int64_t m0 = (int64_t)blockIdx.x * TILE, n0 = (int64_t)blockIdx.y * TILE;
+  T acc[RA][RA];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < RA; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+    for (int b = 0; b < RA; ++b) acc[a][b] = T(0);
   for (int64_t k0 = 0; k0 < K; k0 += 16) {
     // A tile: As[p][i] = op(A)(m0 + i, k0 + p)
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < LD; ++e) {
       const int idx = tid + e * 256;
       int i, p;
-      if (TA) { p = idx & 15; i = idx >> 4; } else { i = idx & 63; p = idx >> 6; }
+      if (TA) { p = idx & 15; i = idx >> 4; } else { i = idx % TILE; p = idx / TILE; }
       const int64_t gi = m0 + i, gp = k0 + p;
       T v = T(0);
       if (gi < M && gp < K) v = TA ? A[gp + gi * lda] : A[gi + gp * lda];
@@ -34,10 +38,10 @@ gemm_kernel(int64_t M, int64_t N, int64_t K, T alpha, const T* __restrict__ A, i
     }
     // B tile: Bs[p][j] = op(B)(k0 + p, n0 + j)
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < LD; ++e) {
       const int idx = tid + e * 256;
       int j, p;
-      if (TB) { j = idx & 63; p = idx >> 6; } else { p = idx & 15; j = idx >> 4; }
+      if (TB) { j = idx % TILE; p = idx / TILE; } else { p = idx & 15; j = idx >> 4; }
       const int64_t gj = n0 + j, gp = k0 + p;
       T v = T(0);
       if (gj < N && gp < K) v = TB ? B[gj + gp * ldb] : B[gp + gj * ldb];
@@ -46,30 +50,51 @@ gemm_kernel(int64_t M, int64_t N, int64_t K, T alpha, const T* __restrict__ A, i
     __syncthreads();
 #pragma unroll
     for (int p = 0; p < 16; ++p) {
-      T av[4], bv[4];
+      T av[RA], bv[RA];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) av[a] = As[p][tx + 16 * a];
+      for (int a = 0; a < RA; ++a) av[a] = As[p][tx + 16 * a];
 #pragma unroll
-      for (int b = 0; b < 4; ++b) bv[b] = Bs[p][ty + 16 * b];
+      for (int b = 0; b < RA; ++b) bv[b] = Bs[p][ty + 16 * b];
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < RA; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        for (int b = 0; b < RA; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int b = 0; b < 4; ++b) {
+  for (int b = 0; b < RA; ++b) {
     const int64_t j = n0 + ty + 16 * b;
     if (j >= N) continue;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
+    for (int a = 0; a < RA; ++a) {
       const int64_t i = m0 + tx + 16 * a;
       if (i >= M) continue;
       T* c = C + i + j * ldc;
       *c = (beta == T(0)) ? alpha * acc[a][b] : alpha * acc[a][b] + beta * *c;
     }
   }
+}
+
+static int g_num_sms = 0;
+static int num_sms() {
+  if (!g_num_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  return g_num_sms;
+}
+
+template <typename T, int TILE>
+static void gemm_launch(bool TA, bool TB, int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t lda,
+                        const T* B, int64_t ldb, T beta, T* C, int64_t ldc, cudaStream_t s) {
+  dim3 grid((unsigned)ceil_div(M, TILE), (unsigned)ceil_div(N, TILE));
+  if (!TA && !TB) gemm_kernel<T, false, false, TILE><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else if (TA && !TB) gemm_kernel<T, true, false, TILE><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else if (!TA && TB) gemm_kernel<T, false, true, TILE><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else gemm_kernel<T, true, true, TILE><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
 }
 
 template <typename T>
@@ -80,12 +105,12 @@ int gemm(char ta, char tb, int64_t M, int64_t N, int64_t K, T alpha, const T* A,
     if (beta == T(0)) return set_zero<T>(C, M, N, ldc, s);
     return scale_cols<T>(C, M, N, ldc, nullptr, s);  // beta must be 0 or 1 here
   }
-  dim3 grid((unsigned)ceil_div(M, 64), (unsigned)ceil_div(N, 64));
   const bool TA = (ta == 'T' || ta == 't'), TB = (tb == 'T' || tb == 't');
-  if (!TA && !TB) gemm_kernel<T, false, false><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-  else if (TA && !TB) gemm_kernel<T, true, false><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-  else if (!TA && TB) gemm_kernel<T, false, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-  else gemm_kernel<T, true, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  // 64-wide tiles when they already give every SM two tiles, 32-wide tiles otherwise
+  if (ceil_div(M, 64) * ceil_div(N, 64) >= 2 * num_sms())
+    gemm_launch<T, 64>(TA, TB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
+  else
+    gemm_launch<T, 32>(TA, TB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
   LYAP_CUDA_TRY(cudaGetLastError());
   lyap_count_launch();
   return LYAP_OK;

@@ -20,6 +20,9 @@ struct EigScratch {
   int* coff = nullptr;       // q + 1
   int* cidx = nullptr;       // q
   int* cinfo = nullptr;      // 4
+  GridBar* bar = nullptr;    // grid barrier of the cooperative Jacobi
+  int* status = nullptr;     // device status word
+  int num_sms = 0;
 };
 
 // H (q x q, ldh, FP64, symmetric; not modified) = Q diag(w) Q^T, w ascending,

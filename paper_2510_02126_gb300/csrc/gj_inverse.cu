@@ -23,19 +23,6 @@ namespace lyap {
 int gj_update_tc(int prec, int n, int k, int bb, int step, const float* Mcur, float* Mnew,
                  const void* Pp, const void* Rt, const int* orig, const int* exps, cudaStream_t s);
 
-template <typename T>
-struct PanelShared {
-  T wv[32];
-  int wi[32];
-  T prow[GJ_BS];
-  T grow[GJ_BS];
-  T prl[GJ_BS];
-  int prow_orig, grow_orig, stop;
-  int rsrc[GJ_BS];
-  float red[32];
-  float cmax[2];
-};
-
 __device__ __forceinline__ void op_store(float* p, float v) { *p = v; }
 __device__ __forceinline__ void op_store(double* p, double v) { *p = v; }
 __device__ __forceinline__ void op_store(__half* p, float v) { *p = __float2half_rn(v); }
@@ -45,14 +32,38 @@ template <typename OP> struct is16 { static constexpr bool value = false; };
 template <> struct is16<__half> { static constexpr bool value = true; };
 template <> struct is16<__nv_bfloat16> { static constexpr bool value = true; };
 
+// Register-resident panel, lane = panel column: CTA `rank` of the cluster owns rows
+// [rank R, rank R + R), R = NW * RPT (NW warps); warp w holds rows base + w + NW i
+// (i < RPT) and lane t holds column t of each of them.  A Gauss-Jordan step is then one
+// warp shuffle (the row's pivot-column entry) and one FMA per held row and lane, and
+// loads and stores of panel rows are 128-byte coalesced.
+//
+// One barrier (CTA or cluster) per column: before it every warp publishes its pivot
+// candidate for the column (value, row, and the whole row) and the owner of the
+// diagonal row g publishes row g; after it every warp reduces the candidates to the
+// pivot p and reads the pivot row and row g directly.  The published slots are
+// double-buffered by column parity, so the writes of column j+1 never meet the reads of
+// column j.  Row interchanges are recorded as the pivot sequence and replayed at the
+// end to give each row its source row in the old matrix.
+template <typename T>
+struct PanelSh {
+  T cv[2][32];          // candidate |value| per warp
+  int ci[2][32];        // candidate row (global), -1 if none
+  T crow[2][32][GJ_BS]; // candidate rows
+  T grow[2][GJ_BS];     // row g before the step
+  int piv[GJ_BS];       // pivot row of each panel column
+  int rsrc[GJ_BS];      // source row (in the old matrix) of pivot row k + t
+  float red[32];
+  float cmax[2];
+};
+
 template <typename T, bool CL>
 __device__ __forceinline__ void panel_sync() {
   if constexpr (CL) cluster_sync_all(); else __syncthreads();
 }
 
-// Block (cluster) wide max of a non-negative float; every thread gets the result.
 template <typename T, bool CL>
-__device__ float panel_max(float v, PanelShared<T>& sh, int C, int slot) {
+__device__ float panel_max2(float v, PanelSh<T>& sh, int C, int slot) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   v = warp_max(v);
   if (lane == 0) sh.red[warp] = v;
@@ -72,194 +83,199 @@ __device__ float panel_max(float v, PanelShared<T>& sh, int C, int slot) {
   return m;
 }
 
-template <typename T, bool CL, typename OP>
-__global__ void __launch_bounds__(GJ_PANEL_THREADS, 1)
+template <typename T, int RPT>
+__device__ __forceinline__ T pick(const T (&v)[RPT], int i) {
+  T r = T(0);
+#pragma unroll
+  for (int u = 0; u < RPT; ++u) r = (u == i) ? v[u] : r;
+  return r;
+}
+
+// Source row of position r after the interchanges (g_0 <-> piv[0]), ..., applied in
+// order: position r ends up holding old row s_0(s_1(... s_{bb-1}(r))).
+__device__ __forceinline__ int replay_swaps(int r, int k, int bb, const int* piv) {
+  int x = r;
+  for (int j = bb - 1; j >= 0; --j) {
+    const int g = k + j, p = piv[j];
+    x = (x == g) ? p : ((x == p) ? g : x);
+  }
+  return x;
+}
+
+template <typename T, int NW, int RPT, bool CL, typename OP>
+__global__ void __launch_bounds__(NW * 32, 1)
 gj_panel_kernel(int n, int k, int step, const T* __restrict__ Mcur, T* __restrict__ Mnew,
                 OP* __restrict__ Pp, OP* __restrict__ Rt, int* __restrict__ orig_out,
                 const int* __restrict__ perm_old, int* __restrict__ perm_new,
                 double* __restrict__ logpiv, int* __restrict__ ipiv, int* __restrict__ status,
                 int* __restrict__ exps) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  PanelShared<T>& sh = *reinterpret_cast<PanelShared<T>*>(smem_raw);
-  const size_t head = (sizeof(PanelShared<T>) + 15) & ~size_t(15);
+  __shared__ PanelSh<T> sh;
   const int C = CL ? (int)gridDim.x : 1;
   const int rank = CL ? (int)cluster_ctarank() : 0;
-  const int R = (n + C - 1) / C;
-  T* panel = reinterpret_cast<T*>(smem_raw + head);
-  int* orig_s = reinterpret_cast<int*>(smem_raw + head + sizeof(T) * (size_t)R * GJ_BS);
+  constexpr int R = NW * RPT;
   const int base = rank * R;
-  const int Rc = max(0, min(R, n - base));
   const int bb = min(GJ_BS, n - k);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int NT = blockDim.x, NW = NT >> 5;
+  const int row0 = base + warp;  // global row of v[0]; v[i] is row row0 + NW i
 
-  for (int idx = tid; idx < Rc * GJ_BS; idx += NT) {
-    const int r = idx / GJ_BS, t = idx - r * GJ_BS;
-    panel[idx] = (t < bb) ? Mcur[(size_t)(base + r) * n + k + t] : T(0);
+  T v[RPT];
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) {
+    const int gr = row0 + NW * i;
+    v[i] = (gr < n && lane < bb) ? Mcur[(size_t)gr * n + k + lane] : T(0);
   }
-  for (int r = tid; r < Rc; r += NT) orig_s[r] = base + r;
-  if (tid == 0) sh.stop = 0;
-  __syncthreads();
+  // per-lane running candidate of this lane's column over the warp's rows >= k
+  T bv = T(-1);
+  int bi = -1;
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) {
+    const int gr = row0 + NW * i;
+    const T a = fabs(v[i]);
+    if (gr < n && gr >= k && (bi < 0 || a > bv)) { bv = a; bi = i; }
+  }
 
   bool bad = false;
+#pragma unroll 1
   for (int j = 0; j < bb; ++j) {
-    const int g = k + j;
-    // (a) local pivot candidate
-    T bv = T(-1);
-    int bi = -1;
-    for (int r = tid; r < Rc; r += NT) {
-      const int gr = base + r;
-      if (gr >= g) {
-        const T v = fabs(panel[r * GJ_BS + j]);
-        if (bi < 0 || v > bv) { bv = v; bi = gr; }
-      }
+    const int g = k + j, buf = j & 1;
+    // (a) publish this warp's candidate for column j and, by its owner, row g
+    const T wv = __shfl_sync(0xffffffffu, bv, j);
+    const int wi = __shfl_sync(0xffffffffu, bi, j);
+    if (wi >= 0) sh.crow[buf][warp][lane] = pick<T, RPT>(v, wi);
+    if (lane == 0) {
+      sh.cv[buf][warp] = wv;
+      sh.ci[buf][warp] = (wi >= 0) ? row0 + NW * wi : -1;
     }
-    warp_argmax(bv, bi);
-    if (lane == 0) { sh.wv[warp] = bv; sh.wi[warp] = bi; }
+    const int og = g / R, lg = g - og * R;
+    if (rank == og && warp == lg % NW) sh.grow[buf][lane] = pick<T, RPT>(v, lg / NW);
     panel_sync<T, CL>();
-    // (b) global pivot: every warp reduces all candidates (identical result everywhere)
+    // (b) pivot: every warp reduces all candidates (the same result everywhere)
     T pv = T(-1);
     int p = -1;
     for (int e = lane; e < C * NW; e += 32) {
       const int cr = e / NW, w = e - cr * NW;
-      T cv;
-      int ci;
+      T cval;
+      int crow;
       if constexpr (CL) {
-        cv = dsmem_ld<T>(dsmem_map(&sh.wv[w], cr));
-        ci = dsmem_ld_s32(dsmem_map(&sh.wi[w], cr));
+        cval = dsmem_ld<T>(dsmem_map(&sh.cv[buf][w], cr));
+        crow = dsmem_ld_s32(dsmem_map(&sh.ci[buf][w], cr));
       } else {
-        cv = sh.wv[w];
-        ci = sh.wi[w];
+        cval = sh.cv[buf][w];
+        crow = sh.ci[buf][w];
       }
-      if (ci >= 0 && (p < 0 || cv > pv || (cv == pv && ci < p))) { pv = cv; p = ci; }
+      if (crow >= 0 && (p < 0 || cval > pv || (cval == pv && crow < p))) { pv = cval; p = crow; }
     }
     warp_argmax(pv, p);
-    if (p < 0 || !(pv > T(0)) || !isfinite((double)pv)) {
+    if (p < 0 || !(pv > T(0)) || !isfinite(pv)) {
       if (tid == 0 && rank == 0)
-        atomicCAS(status, 0, (p >= 0 && isnan((double)pv)) || isinf((double)pv) ? LYAP_ERR_NONFINITE
-                                                                                : LYAP_ERR_SINGULAR);
+        atomicCAS(status, 0, (p >= 0 && (isnan(pv) || isinf(pv))) ? LYAP_ERR_NONFINITE : LYAP_ERR_SINGULAR);
       bad = true;
       break;  // every thread of every CTA takes the same branch
     }
-    // (c) publish the pivot row and the row it displaces
-    const int op = p / R, rp = p - op * R;
-    const int og = g / R, rg = g - og * R;
-    if (rank == op && tid < GJ_BS) sh.prow[tid] = panel[rp * GJ_BS + tid];
-    if (rank == op && tid == 0) sh.prow_orig = orig_s[rp];
-    if (rank == og && tid < GJ_BS) sh.grow[tid] = panel[rg * GJ_BS + tid];
-    if (rank == og && tid == 0) sh.grow_orig = orig_s[rg];
-    panel_sync<T, CL>();
-    const T* prow;
-    if constexpr (CL) {
-      if (warp == 0) sh.prl[lane] = dsmem_ld<T>(dsmem_map(&sh.prow[lane], op));
-      __syncthreads();
-      prow = sh.prl;
-    } else {
-      prow = sh.prow;
-    }
-    const T piv = prow[j];
-    const T inv = T(1) / piv;
-    // (d) row swap + Gauss-Jordan elimination of column j
-    for (int r = tid; r < Rc; r += NT) {
-      const int gr = base + r;
-      T* row = panel + r * GJ_BS;
-      if (gr == g) {
-#pragma unroll 8
-        for (int t = 0; t < GJ_BS; ++t) row[t] = (t == j) ? inv : prow[t] * inv;
-        if (p != g) {
-          int po;
-          if constexpr (CL) po = dsmem_ld_s32(dsmem_map(&sh.prow_orig, op)); else po = sh.prow_orig;
-          orig_s[r] = po;
-        }
-      } else {
-        if (gr == p) {  // p != g here: receives the displaced row g
-#pragma unroll 8
-          for (int t = 0; t < GJ_BS; ++t) {
-            T v;
-            if constexpr (CL) v = dsmem_ld<T>(dsmem_map(&sh.grow[t], og)); else v = sh.grow[t];
-            row[t] = v;
+    const int op = p / R, lp = p - op * R;
+    T prow_t;
+    if constexpr (CL) prow_t = dsmem_ld<T>(dsmem_map(&sh.crow[buf][lp % NW][lane], op));
+    else prow_t = sh.crow[buf][lp % NW][lane];
+    const T pj = __shfl_sync(0xffffffffu, prow_t, j);
+    const T inv = T(1) / pj;
+    // lane j: v <- -f inv (the eliminated column becomes the inverse's column);
+    // other lanes: v <- v - f q_t with q_t = prow_t / pj
+    const T qq = (lane == j) ? inv : prow_t * inv;
+    const T keep = (lane == j) ? T(0) : T(1);
+    // (c) row swap + elimination of column j; candidates of column j+1 on the fly
+    bv = T(-1);
+    bi = -1;
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      const int gr = row0 + NW * i;
+      if (gr < n) {  // warp-uniform
+        if (gr == g) {
+          v[i] = qq;
+        } else {
+          if (gr == p) {  // receives the displaced row g
+            if constexpr (CL) v[i] = dsmem_ld<T>(dsmem_map(&sh.grow[buf][lane], og));
+            else v[i] = sh.grow[buf][lane];
           }
-          int go;
-          if constexpr (CL) go = dsmem_ld_s32(dsmem_map(&sh.grow_orig, og)); else go = sh.grow_orig;
-          orig_s[r] = go;
-        }
-        const T f = row[j];
-        if (f != T(0)) {
-#pragma unroll 8
-          for (int t = 0; t < GJ_BS; ++t) {
-            if (t != j) row[t] -= f * (prow[t] * inv);
-          }
-          row[j] = -f * inv;
+          const T f = __shfl_sync(0xffffffffu, v[i], j);
+          v[i] = fma(-f, qq, v[i] * keep);
+          const T a = fabs(v[i]);
+          if (gr > g && (bi < 0 || a > bv)) { bv = a; bi = i; }
         }
       }
     }
-    if (tid == 0 && rank == 0) {
-      logpiv[g] = log(fabs((double)piv));
-      if (ipiv) ipiv[g] = p;
+    if (tid == 0) {
+      sh.piv[j] = p;
+      if (rank == 0) {
+        logpiv[g] = (double)pj;  // the logarithms are taken after the inversion (pivot_logs)
+        if (ipiv) ipiv[g] = p;
+      }
     }
   }
-  panel_sync<T, CL>();  // all rows final, all orig_s final
+  panel_sync<T, CL>();
   if (bad) return;
 
   // ---- outputs --------------------------------------------------------------
-  for (int idx = tid; idx < Rc * GJ_BS; idx += NT) {
-    const int r = idx / GJ_BS, t = idx - r * GJ_BS;
-    if (t < bb) Mnew[(size_t)(base + r) * n + k + t] = panel[idx];
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) {
+    const int gr = row0 + NW * i;
+    if (gr < n && lane < bb) Mnew[(size_t)gr * n + k + lane] = v[i];
   }
-  for (int r = tid; r < Rc; r += NT) {
-    orig_out[base + r] = orig_s[r];
-    perm_new[base + r] = perm_old[orig_s[r]];
+  for (int r = tid; r < R; r += NW * 32) {
+    const int gr = base + r;
+    if (gr >= n) continue;
+    const int o = replay_swaps(gr, k, bb, sh.piv);
+    orig_out[gr] = o;
+    perm_new[gr] = perm_old[o];
   }
-  // sources of the pivot rows k..k+bb-1
-  if (warp == 0) {
-    int src = -1;
-    if (lane < bb) {
-      const int gr = k + lane, oc = gr / R, rr = gr - oc * R;
-      if constexpr (CL) src = dsmem_ld_s32(dsmem_map(&orig_s[rr], oc)); else src = orig_s[rr];
-    }
-    sh.rsrc[lane] = src;
-  }
+  if (warp == 0) sh.rsrc[lane] = (lane < bb) ? replay_swaps(k + lane, k, bb, sh.piv) : 0;
   __syncthreads();
   const int x0 = (int)((int64_t)rank * n / C), x1 = (int)((int64_t)(rank + 1) * n / C);
+  constexpr int LDO = is16<OP>::value ? GJ_KLD16 : GJ_BS;
 
   float sP = 1.f, sR = 1.f;
   if constexpr (is16<OP>::value) {
     float mp = 0.f;
-    for (int idx = tid; idx < Rc * GJ_BS; idx += NT) {
-      const int r = idx / GJ_BS, t = idx - r * GJ_BS;
-      if (t < bb) {
-        const float v = (float)panel[idx] - ((base + r) == k + t ? 1.f : 0.f);
-        mp = fmaxf(mp, fabsf(v));
-      }
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      const int gr = row0 + NW * i;
+      if (gr < n && lane < bb) mp = fmaxf(mp, fabsf((float)v[i] - (gr == k + lane ? 1.f : 0.f)));
     }
     float mr = 0.f;
-    for (int x = x0 + tid; x < x1; x += NT) {
-      if (x >= k && x < k + bb) continue;
-      for (int t = 0; t < bb; ++t) mr = fmaxf(mr, fabsf((float)Mcur[(size_t)sh.rsrc[t] * n + x]));
+    if (lane < bb) {
+      const T* src = Mcur + (size_t)sh.rsrc[lane] * n;
+      for (int x = x0 + warp; x < x1; x += NW)
+        if (x < k || x >= k + bb) mr = fmaxf(mr, fabsf((float)src[x]));
     }
-    mp = panel_max<T, CL>(mp, sh, C, 0);
-    mr = panel_max<T, CL>(mr, sh, C, 1);
+    mp = panel_max2<T, CL>(mp, sh, C, 0);
+    mr = panel_max2<T, CL>(mr, sh, C, 1);
     const int eP = pow2_exponent(mp), eR = pow2_exponent(mr);
     sP = ldexpf(1.f, -eP);
     sR = ldexpf(1.f, -eR);
     if (tid == 0 && rank == 0) { exps[2 * step] = eP; exps[2 * step + 1] = eR; }
   }
-  constexpr int LDO = is16<OP>::value ? GJ_KLD16 : GJ_BS;
-  for (int idx = tid; idx < Rc * LDO; idx += NT) {
-    const int r = idx / LDO, t = idx - r * LDO;
-    T v = T(0);
-    if (t < bb) v = panel[r * GJ_BS + t] - ((base + r) == k + t ? T(1) : T(0));
-    if constexpr (is16<OP>::value) op_store(&Pp[(size_t)(base + r) * LDO + t], (float)v * sP);
-    else op_store(&Pp[(size_t)(base + r) * LDO + t], v);
+  // P' = panel - I on its diagonal block (lane = column: coalesced rows)
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) {
+    const int gr = row0 + NW * i;
+    if (gr >= n) continue;
+    const T val = (lane < bb) ? v[i] - (gr == k + lane ? T(1) : T(0)) : T(0);
+    if constexpr (is16<OP>::value) {
+      op_store(&Pp[(size_t)gr * LDO + lane], (float)val * sP);
+      op_store(&Pp[(size_t)gr * LDO + 32 + lane], 0.f);
+    } else {
+      op_store(&Pp[(size_t)gr * LDO + lane], val);
+    }
   }
-  for (int x = x0 + tid; x < x1; x += NT) {
-    const bool inpanel = (x >= k && x < k + bb);
-#pragma unroll 4
-    for (int t = 0; t < LDO; ++t) {
-      T v = T(0);
-      if (t < bb && !inpanel) v = Mcur[(size_t)sh.rsrc[t] * n + x];
-      if constexpr (is16<OP>::value) op_store(&Rt[(size_t)x * LDO + t], (float)v * sR);
-      else op_store(&Rt[(size_t)x * LDO + t], v);
+  // R^T[x, t] = pivot row t at column x (lane = t: coalesced rows of R^T)
+  const T* srow = Mcur + (size_t)sh.rsrc[lane] * n;
+  for (int x = x0 + warp; x < x1; x += NW) {
+    const bool use = lane < bb && (x < k || x >= k + bb);
+    const T val = use ? srow[x] : T(0);
+    if constexpr (is16<OP>::value) {
+      op_store(&Rt[(size_t)x * LDO + lane], (float)val * sR);
+      op_store(&Rt[(size_t)x * LDO + 32 + lane], 0.f);
+    } else {
+      op_store(&Rt[(size_t)x * LDO + lane], val);
     }
   }
   if constexpr (CL) cluster_sync_all();  // keep shared memory alive for remote readers
@@ -312,37 +328,47 @@ gj_update_simt(int n, int k, int bb, const T* __restrict__ Mcur, T* __restrict__
   }
 }
 
-int gj_panel_cluster(int n, int elt) {
-  const int64_t bytes = (int64_t)n * (GJ_BS * elt + 4);
-  int C = (int)ceil_div(bytes, GJ_PANEL_SMEM_BUDGET);
-  if (C < 1) C = 1;
-  if (C > n) C = n;
-  return C;
+// Panel geometry (lane = column, NW warps x RPT rows per CTA, C = ceil(n / (NW RPT))
+// CTAs in one cluster, at most 16).  FP32: 16 warps x 32 rows per CTA (128 registers a
+// thread, 32 of them the panel).  FP64 (two registers per value, and FP64
+// arithmetic slow enough that it must spread over many SMs): 16 warps x 4, 8 or 16 rows,
+// the smallest that fits n in 16 CTAs.
+struct PanelGeom { int nw, rpt, C; };
+static PanelGeom panel_geom(int n, int elt) {
+  PanelGeom g;
+  if (elt == 4) {
+    g.nw = 16;
+    g.rpt = 32;
+  } else {
+    g.nw = 16;
+    g.rpt = (n <= 16 * 16 * 4) ? 4 : (n <= 16 * 16 * 8) ? 8 : 16;
+  }
+  g.C = (int)ceil_div(n, (int64_t)g.nw * g.rpt);
+  return g;
 }
 
-template <typename T, bool CL, typename OP>
+int gj_panel_cluster(int n, int elt) { return panel_geom(n, elt).C; }
+
+template <typename T, int NW, int RPT, bool CL, typename OP>
 static int launch_panel(GJWork& W, int k, int step, cudaStream_t s) {
   const int n = W.n;
-  const int C = gj_panel_cluster(n, sizeof(T));
-  if (C > 8) {
+  const int C = panel_geom(n, sizeof(T)).C;
+  if (C > 16 || (!CL && C != 1)) {
     lyap_set_error_message("matrix order too large for the panel cluster", __FILE__, __LINE__);
     return LYAP_ERR_ARG;
   }
-  const int R = (n + C - 1) / C;
-  const size_t head = (sizeof(PanelShared<T>) + 15) & ~size_t(15);
-  const size_t smem = head + sizeof(T) * (size_t)R * GJ_BS + sizeof(int) * (size_t)R;
-  auto kern = gj_panel_kernel<T, CL, OP>;
+  auto kern = gj_panel_kernel<T, NW, RPT, CL, OP>;
   static bool attr_set = false;
-  if (!attr_set) {
-    LYAP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  if (CL && !attr_set) {
+    LYAP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     attr_set = true;
   }
   const T* Mcur = (const T*)W.M[W.cur];
   T* Mnew = (T*)W.M[1 - W.cur];
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(C);
-  cfg.blockDim = dim3(GJ_PANEL_THREADS);
-  cfg.dynamicSmemBytes = smem;
+  cfg.blockDim = dim3(NW * 32);
+  cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   if (CL) {
@@ -360,10 +386,21 @@ static int launch_panel(GJWork& W, int k, int step, cudaStream_t s) {
   return LYAP_OK;
 }
 
+template <typename T, int NW, int RPT, typename OP>
+static int panel_dispatch_g(GJWork& W, int k, int step, cudaStream_t s) {
+  if (gj_panel_cluster(W.n, sizeof(T)) > 1) return launch_panel<T, NW, RPT, true, OP>(W, k, step, s);
+  return launch_panel<T, NW, RPT, false, OP>(W, k, step, s);
+}
 template <typename T, typename OP>
 static int panel_dispatch(GJWork& W, int k, int step, cudaStream_t s) {
-  if (gj_panel_cluster(W.n, sizeof(T)) > 1) return launch_panel<T, true, OP>(W, k, step, s);
-  return launch_panel<T, false, OP>(W, k, step, s);
+  const PanelGeom g = panel_geom(W.n, sizeof(T));
+  if constexpr (sizeof(T) == 4) {
+    return panel_dispatch_g<T, 16, 32, OP>(W, k, step, s);
+  } else {
+    if (g.rpt == 4) return panel_dispatch_g<T, 16, 4, OP>(W, k, step, s);
+    if (g.rpt == 8) return launch_panel<T, 16, 8, true, OP>(W, k, step, s);
+    return launch_panel<T, 16, 16, true, OP>(W, k, step, s);
+  }
 }
 
 template <typename T>
@@ -372,6 +409,31 @@ static int update_simt(GJWork& W, int k, int bb, cudaStream_t s) {
   dim3 grid((unsigned)ceil_div(n, 64), (unsigned)ceil_div(n, 64));
   gj_update_simt<T><<<grid, 256, 0, s>>>(n, k, bb, (const T*)W.M[W.cur], (T*)W.M[1 - W.cur],
                                          (const T*)W.Pp, (const T*)W.Rt, W.orig);
+  LYAP_CUDA_TRY(cudaGetLastError());
+  lyap_count_launch();
+  return LYAP_OK;
+}
+
+__global__ void pivot_log_kernel(double* __restrict__ piv, int n, double* __restrict__ out) {
+  __shared__ double red[32];
+  double t = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double l = log(fabs(piv[i]));
+    piv[i] = l;
+    t += l;
+  }
+  t = warp_sum(t);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    *out = s;
+  }
+}
+
+int pivot_logs(GJWork& W, double* out, cudaStream_t s) {
+  pivot_log_kernel<<<1, 1024, 0, s>>>(W.logpiv, W.n, out);
   LYAP_CUDA_TRY(cudaGetLastError());
   lyap_count_launch();
   return LYAP_OK;

@@ -10,10 +10,6 @@ namespace lyap {
 constexpr int GJ_BS = 32;
 // Row pitch (elements) of the 16-bit panel operands: one 128-byte TMA/UMMA row, upper half zero.
 constexpr int GJ_KLD16 = 64;
-// Threads of the panel kernel.
-constexpr int GJ_PANEL_THREADS = 1024;
-// Shared-memory budget per panel CTA (panel rows x GJ_BS values).
-constexpr int GJ_PANEL_SMEM_BUDGET = 200 * 1024;
 
 // Device workspace of one inversion of order n in working type T (row-major).
 struct GJWork {
@@ -24,7 +20,7 @@ struct GJWork {
   void* Rt = nullptr;    // pivot-row operand, n x GJ_BS (T or 16-bit)
   int* orig = nullptr;   // row gather map of the current step (n)
   int* perm[2] = {nullptr, nullptr};  // composed row permutation (n)
-  double* logpiv = nullptr;  // log|pivot| per column (n)
+  double* logpiv = nullptr;  // pivot of each column (n); log|pivot| after pivot_logs()
   int* ipiv = nullptr;       // pivot row chosen at each column (n)
   int* status = nullptr;     // device status word (0 = ok, else LYAP_ERR_*)
   int* exps = nullptr;       // per-step power-of-two exponents of the 16-bit operands (2 per step)
@@ -39,6 +35,9 @@ struct GJWork {
 // FP64 -> T=double SIMT, FP32 -> T=float SIMT, FP16/BF16 -> T=float working
 // matrix with tcgen05 tensor-core updates on 16-bit operands.
 int gj_invert_run(GJWork& W, int prec, cudaStream_t s);
+
+// Replace the recorded pivots by log|pivot| and write their sum to *out (device).
+int pivot_logs(GJWork& W, double* out, cudaStream_t s);
 
 // Cluster size used by the panel kernel for order n and element size elt.
 int gj_panel_cluster(int n, int elt);

@@ -72,9 +72,10 @@ struct lyap_ctx {
   lyap::Buf store, dmu, dex;
   int store_n = 0, store_prec = -1, store_count = 0, store_e0 = 0;
   size_t store_elt = 0;
-  int64_t store_ld = 0;  // row pitch (elements) of a stored inverse
+  int64_t store_ld = 0;    // row pitch (elements) of a stored inverse
+  int64_t store_rows = 0;  // rows allocated per stored inverse
   // FP64 refinement buffers
-  lyap::Buf F, tau, Tm, TP, H, w, Qh, Csel, Lp, Lm, Zs, Zbest, G, gram, ysol, ybest, ytmp, Lw, Sd, Vs, Lst;
+  lyap::Buf F, tau, Tm, TP, H, w, Qh, Csel, Lp, Lm, Zs, Zbest, G, gram, ysol, ybest, ytmp, Lw, Sd, Vs, Lst, Rtau, Bm, VB;
   // scratch of the QR and eigen kernels
   lyap::QRScratch qr;
   lyap::Buf qrBar, qrStatus, qrCand, qrNorms, qrPiv, qrRdiag, qrWork, qrRank;
@@ -82,6 +83,11 @@ struct lyap_ctx {
   lyap::Buf eigWork32, eigX, eigR, eigS, eigHX, eigE, eigLam, eigRed, eigW, eigPv, eigInt;
   void* hpin = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
+  // phase profiling (opts.profile): events recorded at phase boundaries
+  bool profile = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> marks_phase;
+  size_t marks_used = 0;
 };
 
 namespace lyap {
@@ -89,6 +95,33 @@ namespace lyap {
 using Ctx = lyap_ctx;
 
 static bool is16(int prec) { return prec == LYAP_FP16 || prec == LYAP_BF16; }
+
+// Start of a phase on the context stream (no-op unless profiling).
+static void mark(Ctx& C, int phase) {
+  if (!C.profile) return;
+  if (C.marks_used == C.ev_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    C.ev_pool.push_back(e);
+  }
+  cudaEventRecord(C.ev_pool[C.marks_used], C.s);
+  if (C.marks_phase.size() <= C.marks_used) C.marks_phase.resize(C.marks_used + 1);
+  C.marks_phase[C.marks_used] = phase;
+  ++C.marks_used;
+}
+static void collect_marks(Ctx& C, lyap_info_t* info) {
+  if (!C.profile) return;
+  mark(C, LYAP_PHASE_OTHER);
+  cudaEventSynchronize(C.ev_pool[C.marks_used - 1]);
+  for (size_t i = 0; i + 1 < C.marks_used; ++i) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, C.ev_pool[i], C.ev_pool[i + 1]);
+    const int ph = C.marks_phase[i];
+    info->phase_ms[ph] += ms;
+    info->phase_calls[ph] += 1;
+  }
+  C.marks_used = 0;
+}
 
 // ---------------------------------------------------------------------------
 // small kernels of the Newton step (Eq. (3.1a)-(3.3))
@@ -366,8 +399,8 @@ static int prepare_newton(Ctx& C, int n, int m, int prec) {
   const size_t elt = sizeof(T);
   LYAP_TRY(ensure(C.gjM0, nn * elt));
   LYAP_TRY(ensure(C.gjM1, nn * elt));
-  LYAP_TRY(ensure(C.gjPp, (size_t)n * GJ_BS * elt));
-  LYAP_TRY(ensure(C.gjRt, (size_t)n * GJ_BS * elt));
+  LYAP_TRY(ensure(C.gjPp, (size_t)tc_rows(n) * GJ_KLD16 * 2 + (size_t)n * GJ_BS * elt));
+  LYAP_TRY(ensure(C.gjRt, (size_t)tc_rows(n) * GJ_KLD16 * 2 + (size_t)n * GJ_BS * elt));
   LYAP_TRY(ensure(C.gjOrig, (size_t)n * 4));
   LYAP_TRY(ensure(C.gjPerm0, (size_t)n * 4));
   LYAP_TRY(ensure(C.gjPerm1, (size_t)n * 4));
@@ -382,7 +415,10 @@ static int prepare_newton(Ctx& C, int n, int m, int prec) {
   LYAP_TRY(ensure(C.colsum, (size_t)n * 8));
   LYAP_TRY(ensure(C.Zw, (size_t)n * zcap * elt));
   LYAP_TRY(ensure(C.Zw2, (size_t)n * zcap * elt));
-  LYAP_TRY(ensure(C.Zh, (size_t)n * zcap * 2 + 256));
+  if (C.Zh.cap < (size_t)tc_rows(zcap) * tc_kpitch(n) * 2 + 256) {
+    LYAP_TRY(ensure(C.Zh, (size_t)tc_rows(zcap) * tc_kpitch(n) * 2 + 256));
+    LYAP_CUDA_TRY(cudaMemsetAsync(C.Zh.p, 0, C.Zh.cap, C.s));  // padding rows stay finite
+  }
   LYAP_TRY(ensure(C.eZ, (size_t)zcap * 4));
   LYAP_TRY(ensure(C.yv, (size_t)zcap * 8));
   LYAP_TRY(ensure(C.yv2, (size_t)zcap * 8));
@@ -455,6 +491,11 @@ static int prepare_eig(Ctx& C, int q) {
   C.eig.coff = P<int>(C.eigInt) + q;
   C.eig.cidx = P<int>(C.eigInt) + 2 * q + 1;
   C.eig.cinfo = P<int>(C.eigInt) + 3 * q + 4;
+  LYAP_TRY(ensure(C.qrBar, sizeof(GridBar)));
+  LYAP_TRY(ensure(C.qrStatus, 16));
+  C.eig.bar = P<GridBar>(C.qrBar);
+  C.eig.status = P<int>(C.qrStatus);
+  C.eig.num_sms = C.num_sms;
   return LYAP_OK;
 }
 
@@ -485,12 +526,12 @@ static int invert_current(Ctx& C, const T* Acur, int n, int prec) {
 template <typename T>
 static int factor_product(Ctx& C, int n, int c, int prec, int kk, T* Z) {
   if (is16(prec)) {
-    const void* Xs = (const char*)C.store.p + (size_t)kk * (size_t)n * C.store_ld * C.store_elt;
+    const void* Xs = (const char*)C.store.p + (size_t)kk * (size_t)C.store_rows * C.store_ld * C.store_elt;
     LYAP_TRY(factor_to_16(prec, (const float*)Z, n, c, n, C.Zh.p, P<int>(C.eZ), C.s));
     LYAP_TRY(tc_product(prec, n, c, Xs, P<int>(C.dex) + kk, C.Zh.p, P<int>(C.eZ), (float*)Z + (size_t)c * n, n,
                         C.s));
   } else {
-    const T* Xs = (const T*)((const char*)C.store.p + (size_t)kk * (size_t)n * C.store_ld * C.store_elt);
+    const T* Xs = (const T*)((const char*)C.store.p + (size_t)kk * (size_t)C.store_rows * C.store_ld * C.store_elt);
     // Xs is row-major, i.e. the transpose of a column-major n x n matrix
     LYAP_TRY(gemm<T>('T', 'N', n, c, n, T(1), Xs, n, Z, n, T(0), Z + (size_t)c * n, n, C.s));
   }
@@ -591,20 +632,19 @@ static int newton_run(Ctx& C, int n, int c0, bool ldlt, const NewtonOpts& o, boo
         return LYAP_ERR_NOCONV;
       }
       LYAP_CUDA_TRY(cudaMemsetAsync(C.gj.status, 0, sizeof(int), C.s));
+      mark(C, LYAP_PHASE_INVERT);
       LYAP_TRY(invert_current<T>(C, Acur, n, o.prec));
+      mark(C, LYAP_PHASE_NEWTON);
       const T* X = (const T*)C.gj.M[C.gj.cur];
       const int* perm = C.gj.perm[C.gj.cur];
       pinv_kernel<<<nblk(n), 256, 0, C.s>>>(perm, P<int>(C.pinv), n);
       lyap_count_launch();
       LYAP_TRY(sumsq<T>(X, n, n, n, &st->ssX, P<double>(C.part), C.s));
       LYAP_TRY(maxabs<T>(X, n, n, n, &st->maxX, P<double>(C.part), C.s));
-      if (o.scaling == LYAP_SCALE_DET) {
-        sum_vec_kernel<<<1, 32, 0, C.s>>>(C.gj.logpiv, n, &st->logdet);
-        lyap_count_launch();
-      }
+      if (o.scaling == LYAP_SCALE_DET) LYAP_TRY(pivot_logs(C.gj, &st->logdet, C.s));
       newton_mu_kernel<<<1, 1, 0, C.s>>>(st, n, o.scaling, is16(o.prec) ? 1 : 0);
       lyap_count_launch();
-      void* slot = (char*)C.store.p + (size_t)kk * (size_t)n * C.store_ld * C.store_elt;
+      void* slot = (char*)C.store.p + (size_t)kk * (size_t)C.store_rows * C.store_ld * C.store_elt;
       const unsigned nb = RED_BLOCKS;
       switch (o.prec) {
         case LYAP_FP64:
@@ -647,6 +687,7 @@ static int newton_run(Ctx& C, int n, int c0, bool ldlt, const NewtonOpts& o, boo
       lyap_set_error_message("Newton factor exceeds its capacity", __FILE__, __LINE__);
       return LYAP_ERR_CAPACITY;
     }
+    mark(C, LYAP_PHASE_FACTOR);
     LYAP_TRY(factor_product<T>(C, n, c, o.prec, kk, Z));
     factor_scale_kernel<T><<<ldlt ? 1 : nblk((int64_t)n * 2 * c), 256, 0, C.s>>>(Z, n, n, c, P<double>(C.dmu) + kk,
                                                                                 ldlt ? 1 : 0, y);
@@ -654,6 +695,7 @@ static int newton_run(Ctx& C, int n, int c0, bool ldlt, const NewtonOpts& o, boo
     lyap_count_launch();
     c *= 2;
     if ((double)c > o.rho * (double)n) {
+      mark(C, LYAP_PHASE_COMPRESS);
       int r = 0;
       if (!ldlt) {
         LYAP_TRY(qrcp_truncate<T>(Z, n, c, n, o.rank_tol, C.qr, C.s));
@@ -663,6 +705,7 @@ static int newton_run(Ctx& C, int n, int c0, bool ldlt, const NewtonOpts& o, boo
       }
       c = r;
     }
+    mark(C, LYAP_PHASE_OTHER);
     if (compute) {
       NewtonState hst;
       LYAP_TRY(sync_read(C, st, &hst, sizeof(NewtonState)));
@@ -785,13 +828,14 @@ int lyap_ctx_destroy(lyap_ctx_t* C) {
                 &C->A1, &C->pinv, &C->colsum, &C->Zw, &C->Zw2, &C->Zh, &C->eZ, &C->yv, &C->yv2, &C->store,
                 &C->dmu, &C->dex, &C->F, &C->tau, &C->Tm, &C->TP, &C->H, &C->w, &C->Qh, &C->Csel, &C->Lp,
                 &C->Lm, &C->Zs, &C->Zbest, &C->G, &C->gram, &C->ysol, &C->ybest, &C->ytmp, &C->Lw, &C->Sd,
-                &C->Vs, &C->Lst, &C->qrBar, &C->qrStatus, &C->qrCand, &C->qrNorms, &C->qrPiv, &C->qrRdiag, &C->qrWork,
+                &C->Vs, &C->Lst, &C->Rtau, &C->Bm, &C->VB, &C->qrBar, &C->qrStatus, &C->qrCand, &C->qrNorms, &C->qrPiv, &C->qrRdiag, &C->qrWork,
                 &C->qrRank, &C->eigWork32, &C->eigX, &C->eigR, &C->eigS, &C->eigHX, &C->eigE, &C->eigLam,
                 &C->eigRed, &C->eigW, &C->eigPv, &C->eigInt};
   for (Buf* b : all) free_buf(*b);
   if (C->hpin) cudaFreeHost(C->hpin);
   if (C->e0) cudaEventDestroy(C->e0);
   if (C->e1) cudaEventDestroy(C->e1);
+  for (cudaEvent_t e : C->ev_pool) cudaEventDestroy(e);
   delete C;
   return LYAP_OK;
 }
@@ -825,8 +869,7 @@ int lyap_invert(lyap_ctx_t* C, const double* A, int64_t n, int64_t lda, int prec
     unpermute_kernel<float><<<nblk(n * n), 256, 0, C->s>>>((const float*)W.M[W.cur], W.perm[W.cur], ni, Ainv, ldai);
   lyap_count_launch();
   double* ld = P<double>(C->scal);
-  sum_vec_kernel<<<1, 32, 0, C->s>>>(W.logpiv, ni, ld);
-  lyap_count_launch();
+  LYAP_TRY(pivot_logs(W, ld, C->s));
   LYAP_CUDA_TRY(cudaGetLastError());
   struct { double ld; } h;
   LYAP_TRY(sync_read(*C, ld, &h, sizeof(h)));
@@ -936,8 +979,12 @@ static int newton_solve(Ctx& C, const Problem& pb, const double* Lr, int mr, con
   const size_t nn = (size_t)n * n;
   if (compute) {
     const size_t selt = (o.u_s == LYAP_FP64) ? 8 : (o.u_s == LYAP_FP32 ? 4 : 2);
-    C.store_ld = (selt == 2) ? ceil_div(n, 8) * 8 : n;  // 16-byte row pitch for the TMA operand
-    LYAP_TRY(ensure(C.store, (size_t)no.kmax * (size_t)n * C.store_ld * selt));
+    // 16-bit inverses are tensor-core A operands: row pitch and row count follow tc_kpitch / tc_rows
+    C.store_ld = (selt == 2) ? tc_kpitch(n) : n;
+    C.store_rows = (selt == 2) ? tc_rows(n) : n;
+    LYAP_TRY(ensure(C.store, (size_t)no.kmax * (size_t)C.store_rows * C.store_ld * selt));
+    if (selt == 2 && (C.store_ld != n || C.store_rows != n))  // K padding must read as zero
+      LYAP_CUDA_TRY(cudaMemsetAsync(C.store.p, 0, (size_t)no.kmax * C.store_rows * C.store_ld * selt, C.s));
     C.store_elt = selt;
     C.store_n = n;
     C.store_prec = o.u_s;
@@ -1025,6 +1072,7 @@ static int res_fac(Ctx& C, const Problem& pb, const double* Lw, const double* sd
                    const double* y, bool ldlt, double eta_r, bool want_split, ResOut* out) {
   const int n = pb.n, m = pb.m;
   const int q = 2 * c + m;
+  mark(C, LYAP_PHASE_RESFAC);
   LYAP_TRY(ensure(C.F, (size_t)n * q * 8 + 64));
   LYAP_TRY(ensure(C.tau, (size_t)(q + 8) * 8));
   double* F = P<double>(C.F);
@@ -1061,19 +1109,50 @@ static int res_fac(Ctx& C, const Problem& pb, const double* Lw, const double* sd
   out->resF = hres[1];
   out->rp = out->rm = 0;
   if (!want_split) return LYAP_OK;
-  // eigen-split of H (FP32 accuracy suffices: the split is truncated at eta_r >> u_fp32)
+  // eigen-split of H (FP32 accuracy suffices: the split is truncated at eta_r >> u_fp32).
+  // Large cores: the range of H is first found by QR with column pivoting truncated at
+  // eta_r / 10 (everything dropped lies far below the truncation level of the split), and
+  // the eigenpairs come from the Rayleigh-Ritz matrix on that range.
   LYAP_TRY(ensure(C.w, (size_t)kr * 8 + 64));
   LYAP_TRY(ensure(C.Qh, (size_t)kr * kr * 8 + 64));
   LYAP_TRY(ensure(C.Csel, (size_t)kr * kr * 8 + 64));
-  LYAP_TRY(prepare_eig(C, kr));
-  LYAP_TRY(sym_eig(P<double>(C.H), kr, kr, P<double>(C.w), P<double>(C.Qh), kr, 0, C.eig, C.s));
+  int neig = kr;
+  if (kr > 160) {
+    double* Zr = P<double>(C.Csel);
+    LYAP_TRY((copy_cast<double, double>(P<double>(C.H), kr, kr, kr, Zr, kr, 1.0, C.s)));
+    LYAP_TRY(qrcp_truncate<double>(Zr, kr, kr, kr, 0.1 * eta_r, C.qr, C.s));
+    int r = 0;
+    LYAP_TRY(sync_read(C, C.qr.rank, &r, sizeof(int)));
+    r = std::max(r, 1);
+    LYAP_TRY(ensure(C.Rtau, (size_t)(r + 8) * 8));
+    LYAP_TRY(ensure(C.Bm, (size_t)r * r * 8 + 64));
+    LYAP_TRY(ensure(C.VB, (size_t)r * r * 8 + 64));
+    LYAP_TRY(householder_qr<double>(Zr, kr, r, kr, P<double>(C.Rtau), C.qr, C.s));
+    LYAP_TRY(set_identity<double>(P<double>(C.Bm), r, r, C.s));
+    double* Qb = P<double>(C.TP);
+    LYAP_TRY(apply_q<double>(Zr, kr, r, kr, P<double>(C.Rtau), P<double>(C.Bm), r, r, Qb, kr, C.s));
+    double* HQ = P<double>(C.Tm);
+    LYAP_TRY(gemm<double>('N', 'N', kr, r, kr, 1.0, P<double>(C.H), kr, Qb, kr, 0.0, HQ, kr, C.s));
+    LYAP_TRY(gemm<double>('T', 'N', r, r, kr, 1.0, Qb, kr, HQ, kr, 0.0, P<double>(C.Bm), r, C.s));
+    LYAP_TRY(prepare_eig(C, r));
+    mark(C, LYAP_PHASE_EIG);
+    LYAP_TRY(sym_eig(P<double>(C.Bm), r, r, P<double>(C.w), P<double>(C.VB), r, 0, C.eig, C.s));
+    mark(C, LYAP_PHASE_RESFAC);
+    LYAP_TRY(gemm<double>('N', 'N', kr, r, r, 1.0, Qb, kr, P<double>(C.VB), r, 0.0, P<double>(C.Qh), kr, C.s));
+    neig = r;
+  } else {
+    LYAP_TRY(prepare_eig(C, kr));
+    mark(C, LYAP_PHASE_EIG);
+    LYAP_TRY(sym_eig(P<double>(C.H), kr, kr, P<double>(C.w), P<double>(C.Qh), kr, 0, C.eig, C.s));
+    mark(C, LYAP_PHASE_RESFAC);
+  }
   int* sel = P<int>(C.scal) + 64;
-  select_kernel<<<1, 32, 0, C.s>>>(P<double>(C.w), kr, eta_r, 0, sel, sc + 30);
+  select_kernel<<<1, 32, 0, C.s>>>(P<double>(C.w), neig, eta_r, 0, sel, sc + 30);
   lyap_count_launch();
   int hs[2];
   LYAP_TRY(sync_read(C, sel, hs, sizeof(hs)));
   const int nneg = hs[0], pos = hs[1];
-  const int npos = kr - pos;
+  const int npos = neig - pos;
   double* Cs = P<double>(C.Csel);
   if (!ldlt) {
     LYAP_TRY(ensure(C.Lp, (size_t)n * std::max(npos, 1) * 8 + 64));
@@ -1122,6 +1201,7 @@ static int res_fac(Ctx& C, const Problem& pb, const double* Lw, const double* sd
 static int sol_upt(Ctx& C, int n, int qg, int cneg_start, const double* ups, bool psd_keep_positive,
                    double eta_s, double* Zout, double* yout, int* r_out) {
   double* G = P<double>(C.G);
+  mark(C, LYAP_PHASE_SOLUPT);
   LYAP_TRY(ensure(C.tau, (size_t)(qg + 8) * 8));
   LYAP_CUDA_TRY(cudaMemsetAsync(C.qr.status, 0, sizeof(int), C.s));
   LYAP_TRY(householder_qr<double>(G, n, qg, n, P<double>(C.tau), C.qr, C.s));
@@ -1139,7 +1219,9 @@ static int sol_upt(Ctx& C, int n, int qg, int cneg_start, const double* ups, boo
   LYAP_TRY(gemm<double>('N', 'T', kr, kr, qg, 1.0, P<double>(C.TP), kr, P<double>(C.Tm), kr, 0.0, P<double>(C.H), kr,
                         C.s));
   LYAP_TRY(prepare_eig(C, kr));
+  mark(C, LYAP_PHASE_EIG);
   LYAP_TRY(sym_eig(P<double>(C.H), kr, kr, P<double>(C.w), P<double>(C.Qh), kr, 1, C.eig, C.s));
+  mark(C, LYAP_PHASE_SOLUPT);
   int* sel = P<int>(C.scal) + 64;
   select_kernel<<<1, 32, 0, C.s>>>(P<double>(C.w), kr, eta_s, 0, sel, P<double>(C.scal) + 31);
   lyap_count_launch();
@@ -1345,8 +1427,13 @@ static int solve_entry(lyap_ctx_t* C, const double* A, int64_t n, int64_t lda, c
   lyap_info_t* inf = info ? info : &local;
   memset(inf, 0, sizeof(*inf));
   const int64_t l0 = g_launches;
+  C->profile = opts->profile != 0;
+  C->marks_used = 0;
   cudaEventRecord(C->e0, C->s);
+  mark(*C, LYAP_PHASE_OTHER);
   int st = solve_common(*C, pb, *opts, refine, Z, ldz, z_cap, D, rank_out, inf);
+  collect_marks(*C, inf);
+  C->profile = false;
   cudaEventRecord(C->e1, C->s);
   cudaEventSynchronize(C->e1);
   float ms = 0.f;

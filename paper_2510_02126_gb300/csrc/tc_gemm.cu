@@ -341,8 +341,10 @@ int tc_status_read(int* out) {
 int gj_update_tc(int prec, int n, int k, int bb, int step, const float* Mcur, float* Mnew, const void* Pp,
                  const void* Rt, const int* orig, const int* exps, cudaStream_t s) {
   CUtensorMap a, b;
-  LYAP_TRY(cached_map(g_cache, 16, Pp, prec, n, GJ_KLD16, GJ_KLD16, &a));
-  LYAP_TRY(cached_map(g_cache, 16, Rt, prec, n, GJ_KLD16, GJ_KLD16, &b));
+  // the operand buffers hold at least TC_BM rows (tc_rows), so the 128-row box never exceeds the map
+  const int rows = tc_rows(n);
+  LYAP_TRY(cached_map(g_cache, 16, Pp, prec, rows, GJ_KLD16, GJ_KLD16, &a));
+  LYAP_TRY(cached_map(g_cache, 16, Rt, prec, rows, GJ_KLD16, GJ_KLD16, &b));
   EpiGJ eg{Mcur, Mnew, orig, exps, n, k, bb, step};
   EpiProd ep{};
   return launch_tc(0, prec, a, b, n, n, GJ_KLD16, eg, ep, s);
@@ -352,9 +354,11 @@ int tc_product(int prec, int n, int c, const void* Xs, const int* eX, const void
                int64_t ldy, cudaStream_t s) {
   if (c <= 0) return LYAP_OK;
   CUtensorMap a, b;
-  const int64_t ldk = ceil_div(n, 8) * 8;  // row pitch of Zh (16-byte aligned)
-  LYAP_TRY(cached_map(g_cache, 16, Xs, prec, n, n, n, &a));
-  LYAP_TRY(cached_map(g_cache, 16, Zh, prec, c, n, ldk, &b));
+  const int64_t ldk = tc_kpitch(n);  // row pitch of Zh and of the stored inverses
+  // maps cover at least one full 128 x 64 box; the padding of both operands is zero (K)
+  // or outside the stored output (M, N), see tc_rows / tc_kpitch
+  LYAP_TRY(cached_map(g_cache, 16, Xs, prec, tc_rows(n), std::max<int64_t>(n, TC_BK), ldk, &a));
+  LYAP_TRY(cached_map(g_cache, 16, Zh, prec, tc_rows(c), std::max<int64_t>(n, TC_BK), ldk, &b));
   EpiGJ eg{};
   EpiProd ep{Y, ldy, eX, eZ, n, c};
   return launch_tc(1, prec, a, b, n, c, n, eg, ep, s);
@@ -387,7 +391,7 @@ __global__ void factor16_kernel(const float* __restrict__ Z, int n, int c, int64
 
 int factor_to_16(int prec, const float* Z, int n, int c, int64_t ld, void* Zh, int* eZ, cudaStream_t s) {
   if (c <= 0) return LYAP_OK;
-  const int64_t ldk = ceil_div(n, 8) * 8;
+  const int64_t ldk = tc_kpitch(n);
   if (prec == LYAP_BF16) factor16_kernel<__nv_bfloat16><<<c, 256, 0, s>>>(Z, n, c, ld, (__nv_bfloat16*)Zh, ldk, eZ);
   else factor16_kernel<__half><<<c, 256, 0, s>>>(Z, n, c, ld, (__half*)Zh, ldk, eZ);
   LYAP_CUDA_TRY(cudaGetLastError());

@@ -4,6 +4,13 @@
 
 namespace lyap {
 
+// Layout rules of the 16-bit tensor-core operands.  Every operand buffer holds at least
+// 128 rows (one TMA box) and a K pitch of at least 64 elements (one 128-byte swizzle row),
+// so that small problems never encode a map smaller than its box.  Rows beyond the
+// problem only feed outputs that the epilogues discard; K padding must be zero.
+inline int64_t tc_rows(int64_t rows) { return rows < 128 ? 128 : rows; }
+inline int64_t tc_kpitch(int64_t k) { const int64_t p = (k + 7) / 8 * 8; return p < 64 ? 64 : p; }
+
 // Gauss-Jordan trailing update on 16-bit operands (prec = LYAP_FP16 / LYAP_BF16):
 //   Mnew[i, x] = Mcur[orig[i], x] + 2^(eP+eR) sum_t Pp[i, t] Rt[x, t]   for x outside [k, k+bb)
 // Pp, Rt: n x 32 (K-major, 16-bit, scaled by 2^-eP / 2^-eR, exponents in exps[2 step .. 2 step+1]).

