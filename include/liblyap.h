@@ -181,6 +181,28 @@ int lyap_invert(lyap_ctx_t* ctx, const double* A, int64_t n, int64_t lda, int pr
                 double* Ainv, int64_t ldai, int32_t* ipiv, double* logabsdet);
 
 /*
+ * lyap_invert without any device allocation (the paper has no counterpart: this entry
+ * point serves callers that may not allocate device memory at all -- code running
+ * under a fixed, pre-reserved memory budget, or inside a framework whose allocator
+ * must not see foreign cudaMalloc/cudaFree calls).  Same operation, kernels and
+ * results as lyap_invert at prec LYAP_FP64 or LYAP_FP32, for n <= LYAP_NOALLOC_MAX_N.
+ *   A, Ainv, ipiv  DEVICE pointers as in lyap_invert (ipiv may be NULL)
+ *   logabsdet      optional HOST double, or NULL
+ *   stream         cudaStream_t to run on (NULL = legacy default stream)
+ * Workspace: one static __device__ array of about 4.4 MiB inside this library,
+ * sized for n = LYAP_NOALLOC_MAX_N in FP64; its address is looked up once per
+ * device, with that device current, on the first call made on that device.  The
+ * call synchronizes `stream` to read the status word and log|det|, so it cannot
+ * be captured into a CUDA graph.  Calls on the same device share the workspace:
+ * they must not overlap (serialize them on one stream or host thread).
+ * Errors: LYAP_ERR_ARG for n > LYAP_NOALLOC_MAX_N, another prec, bad sizes or
+ * NULL pointers (nothing is launched); otherwise as lyap_invert.
+ */
+#define LYAP_NOALLOC_MAX_N 512
+int lyap_invert_noalloc(const double* A, int64_t n, int64_t lda, int prec, double* Ainv,
+                        int64_t ldai, int32_t* ipiv, double* logabsdet, void* stream);
+
+/*
  * RankTruncChol (Sec. 3.2): QR with column pivoting of Z^T, truncated at the first
  * r with ||S_r||_F <= tol * |r_11|, returned as Pi [T C]^T (n x r), overwriting the
  * leading r columns of Z (FP64 arithmetic).  *rank_out receives r.

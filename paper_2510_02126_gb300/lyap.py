@@ -78,6 +78,7 @@ SIGNATURES = {
     "lyap_residual": (C.c_int, [_P, _P, _I64, _I64, _P, _I64, _I64, _P, _I64, _P, _I64, _I64, _P,
                                 C.POINTER(_D)]),
     "lyap_invert": (C.c_int, [_P, _P, _I64, _I64, C.c_int, _P, _I64, _P, C.POINTER(_D)]),
+    "lyap_invert_noalloc": (C.c_int, [_P, _I64, _I64, C.c_int, _P, _I64, _P, C.POINTER(_D), _P]),
     "lyap_rank_trunc": (C.c_int, [_P, _P, _I64, _I64, _I64, _D, C.POINTER(_I64)]),
     "lyap_sym_eig": (C.c_int, [_P, _P, _I64, _I64, _P, _P, _I64, C.c_int]),
     "lyap_last_error": (C.c_char_p, []),
@@ -251,6 +252,26 @@ def invert(A, prec="fp64"):
     return Ai, ipiv, ld.value
 
 
+NOALLOC_MAX_N = 512  # LYAP_NOALLOC_MAX_N
+
+
+def invert_noalloc(A, prec="fp64", out=None, ipiv=None):
+    """lyap_invert through the entry point that allocates no device memory (FP64/FP32,
+    n <= NOALLOC_MAX_N).  `out` / `ipiv` may be preallocated (column-major n x n FP64,
+    int32[n]); returns (Ainv, ipiv, logabsdet)."""
+    lib = load()
+    A = _cm(A)
+    n = A.shape[0]
+    Ai = cm_empty(n, n, A.device) if out is None else out
+    if ipiv is None:
+        ipiv = torch.empty(n, dtype=torch.int32, device=A.device)
+    ld = _D(0.0)
+    _check(lib.lyap_invert_noalloc(_P(A.data_ptr()), n, n, PREC[prec] if isinstance(prec, str) else prec,
+                                   _P(Ai.data_ptr()), n, _P(ipiv.data_ptr()), C.byref(ld), _P(_stream())),
+           allow_warn=False)
+    return Ai, ipiv, ld.value
+
+
 def rank_trunc(Z, tol: float):
     """RankTruncChol: QR with column pivoting of Z^T; returns Pi [T C]^T (n x r)."""
     ctx = context()
@@ -282,5 +303,6 @@ lyap_solve_ir = solve_ir
 lyap_sign_solve = sign_solve
 lyap_residual = residual
 lyap_invert = invert
+lyap_invert_noalloc = invert_noalloc
 lyap_rank_trunc = rank_trunc
 lyap_sym_eig = sym_eig
