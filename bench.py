@@ -243,26 +243,47 @@ def run_ours(args):
     ms_e2e, infos_e2e = timed(e2e_step, max(1, min(args.steps, 3)), 1)
     ok_e2e = all(i.converged for i in infos_e2e)
 
-    # roofline of the dominant phase, from CUDA events recorded by the library on this stream
+    # roofline of the dominant phase, from CUDA events the library records on this stream
+    # and the algorithmic flops it counts per phase
     pk, pk_kind = peaks()
-    phase = {k: 0.0 for k in lyap.PHASES}
-    calls = {k: 0 for k in lyap.PHASES}
+    phase = {k: 0.0 for k in lyap.PHASES if not k.startswith("spare")}
+    calls = dict.fromkeys(phase, 0.0)
+    flops = dict.fromkeys(phase, 0.0)
     for i in infos_ir:
         dd = i.as_dict()
-        for k in lyap.PHASES:
+        for k in phase:
             phase[k] += dd["phase_ms"][k] / len(infos_ir)
             calls[k] += dd["phase_calls"][k] / len(infos_ir)
-    dom = max(phase, key=phase.get)
+            flops[k] += dd["phase_flops"][k] / len(infos_ir)
     n_inv = infos_ir[0].n_inversions
-    inv_ms = phase["invert"] / max(1, n_inv)
-    inv_tflops = 2.0 * n ** 3 / (inv_ms * 1e-3) / 1e12 if inv_ms > 0 else 0.0
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
     peak_tc = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
-    roofline = {"kernel": "gj_invert (panel + tcgen05 trailing update), one n x n inversion",
-                "bound": "tensor", "achieved": inv_tflops, "peak": peak_tc, "unit": "TFLOP/s",
-                "frac": inv_tflops / peak_tc, "traffic": None,
-                "work": f"2 n^3 = {2 * n ** 3:.3e} flop per inversion; {n_inv} inversions per solve",
-                "peak_kind": f"{pk_kind} bf16 sustained (FP16 has the same nominal dense rate)",
-                "dominant_phase": dom, "phase_ms_per_solve": phase, "phase_calls_per_solve": calls}
+    # peaks per phase: FP16 tensor (measured BF16 sustained; same nominal dense rate),
+    # FP32 SIMT derived from 152 SMs x 128 FP32 lanes x 2 flop x SM clock, FP64 nominal
+    kinds = {
+        "invert": ("tensor", peak_tc, f"{pk_kind} bf16 sustained TFLOP/s (FP16 has the same nominal dense rate)",
+                   "gj_panel_kernel + tc_gemm_kernel (blocked Gauss-Jordan, tcgen05 trailing update)",
+                   "2 n^3 flop per inversion"),
+        "eig": ("alu", 152 * 128 * 2 * sm_mhz * 1e6 / 1e12,
+                f"derived FP32 SIMT: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock under load)",
+                "bjac_kernel (FP32 two-sided block Jacobi) / jacobi_kernel (q <= 160)",
+                "9 q^3 flop per eigendecomposition (symmetric QR with eigenvectors, Golub-Van Loan)"),
+        "eig_refine": ("alu", 1.25, "nominal FP64 1.25 TFLOP/s (GB300)",
+                       "gemm_kernel<double> (Ogita-Aishima refinement, Newton-Schulz)", "2 m n k flop per GEMM"),
+    }
+    def roof(k):
+        bound, peak, peak_kind, kern, work = kinds[k]
+        ach = flops[k] / (phase[k] * 1e-3) / 1e12 if phase[k] > 0 else 0.0
+        return {"kernel": kern, "phase": k, "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak if peak else None, "traffic": None, "peak_kind": peak_kind,
+                "work": f"{work}; {flops[k]:.3e} flop and {phase[k]:.1f} ms per solve in this phase"}
+    dom = max(phase, key=phase.get)
+    dom_k = max(kinds, key=lambda k: phase[k])
+    roofline = roof(dom_k)
+    roofline.update({"dominant_phase": dom, "phase_ms_per_solve": phase, "phase_calls_per_solve": calls,
+                     "phase_flops_per_solve": flops})
+    roofline_inv = roof("invert")
+    roofline_inv["work"] += f"; {n_inv} inversions per solve"
 
     launches = int(sum(i.kernel_launches for i in infos_ir))
     line = {
@@ -280,6 +301,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(A_np.nbytes + L_np.nbytes), "d2h_bytes_per_step": int(e2e_step.out_bytes)},
         "gpu_launches": launches,
         "roofline": roofline,
+        "roofline_inversion": roofline_inv,
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
@@ -290,6 +312,42 @@ def run_ours(args):
     return 0
 
 
+def run_case(args):
+    """Small single-kernel workloads for profiler captures (no timing line is printed):
+    invert:<prec>:<n>   two lyap_invert calls on a seeded well-conditioned matrix
+    eig:<q>             two lyap_sym_eig calls (FP64-refined) on a seeded indefinite core
+                        H = T P T^T (T upper triangular, P = diag(+-1)), the shape of the
+                        residual cores of the refinement
+    solve:<u_s>         one lyap_solve_ir of the benchmark workload"""
+    import numpy as np
+    import torch
+    from paper_2510_02126_gb300 import lyap
+    dev = torch.device("cuda:0")
+    kind, *rest = args.case.split(":")
+    g = np.random.default_rng(20251002)
+    if kind == "invert":
+        prec, n = rest[0], int(rest[1])
+        A = torch.tensor(g.standard_normal((n, n)) + 2.0 * np.sqrt(n) * np.eye(n), device=dev)
+        for _ in range(2):
+            lyap.invert(A, prec)
+    elif kind == "eig":
+        q = int(rest[0])
+        T = np.triu(g.standard_normal((q, q)))
+        P = np.where(np.arange(q) % 3 == 0, -1.0, 1.0)
+        H = torch.tensor((T * P[None, :]) @ T.T, device=dev)
+        for _ in range(2):
+            lyap.sym_eig(H, refine=True)
+    elif kind == "solve":
+        d = make_problem()
+        lyap.solve_ir(torch.tensor(d["A"], device=dev), torch.tensor(d["L"], device=dev), u_s=rest[0], tau_ir=TAU,
+                      imax=10)
+    else:
+        raise SystemExit(f"unknown case {args.case}")
+    torch.cuda.synchronize()
+    print(f"case {args.case} done")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -297,7 +355,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default=None, help="profiler workload, e.g. invert:fp16:1024, eig:500, solve:fp16")
     args = ap.parse_args()
+    if args.case:
+        return run_case(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

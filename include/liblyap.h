@@ -83,17 +83,20 @@ typedef struct {
   int reserved[7];
 } lyap_opts_t;
 
-/* Phases reported in lyap_info_t.phase_ms / phase_calls when opts.profile = 1. */
+/* Phases reported in lyap_info_t.phase_ms / phase_calls / phase_flops when
+ * opts.profile = 1 (LYAP_NUM_PHASES slots; the unused ones stay zero). */
 enum {
   LYAP_PHASE_INVERT = 0,   /* n x n inversions (panel + trailing-update kernels) */
   LYAP_PHASE_NEWTON = 1,   /* Newton scalar/epilogue kernels (scaling, A_{k+1}, stop test) */
   LYAP_PHASE_FACTOR = 2,   /* factor products A_k^{-1} Z_k and their scaling */
   LYAP_PHASE_COMPRESS = 3, /* rank truncation inside the Newton iteration */
   LYAP_PHASE_RESFAC = 4,   /* residual factorisation without its eigensolver (A Z, QR, core matrix) */
-  LYAP_PHASE_EIG = 5,      /* symmetric eigensolvers */
+  LYAP_PHASE_EIG = 5,      /* FP32 Jacobi stage of the symmetric eigensolver */
   LYAP_PHASE_SOLUPT = 6,   /* projected solution update without its eigensolver */
-  LYAP_PHASE_OTHER = 7
+  LYAP_PHASE_OTHER = 7,
+  LYAP_PHASE_EIG_REFINE = 8 /* FP64 refinement stage of the symmetric eigensolver */
 };
+#define LYAP_NUM_PHASES 12
 
 typedef struct {
   int status;           /* same value as returned */
@@ -111,8 +114,12 @@ typedef struct {
   double mu[64];        /* Newton scaling parameters mu_0, mu_1, ... */
   int64_t kernel_launches; /* CUDA kernels launched by this call */
   double device_ms;     /* device time of the call (CUDA events on the context stream) */
-  double phase_ms[8];   /* per-phase device time (opts.profile = 1), LYAP_PHASE_* */
-  int64_t phase_calls[8];
+  double phase_ms[LYAP_NUM_PHASES];    /* per-phase device time (opts.profile = 1), LYAP_PHASE_* */
+  int64_t phase_calls[LYAP_NUM_PHASES];/* intervals timed per phase */
+  double phase_flops[LYAP_NUM_PHASES]; /* algorithmic flops per phase: 2 n^3 per inversion;
+                                          9 q^3 per FP32 Jacobi eigendecomposition (the
+                                          symmetric QR count with eigenvectors, Golub-Van Loan);
+                                          2 m n k per FP64 GEMM of the refinement */
 } lyap_info_t;
 
 /* Fill *o with the paper's defaults (u_s = FP16).  Returns LYAP_OK. */

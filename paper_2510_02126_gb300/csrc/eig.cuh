@@ -6,7 +6,7 @@
 namespace lyap {
 
 struct EigScratch {
-  float* work32 = nullptr;   // 2 q^2 floats (used when the matrix does not fit shared memory)
+  float* work32 = nullptr;   // bjac_work_floats(q) floats (block Jacobi workspace)
   double* X = nullptr;       // q^2 each
   double* R = nullptr;
   double* S = nullptr;
@@ -15,7 +15,7 @@ struct EigScratch {
   double* W = nullptr;       // q^2 (cluster rotations)
   double* lam = nullptr;     // q
   double* pv = nullptr;      // 2 q (power iteration vectors)
-  double* red = nullptr;     // >= 16 + RED_BLOCKS doubles
+  double* red = nullptr;     // >= 16 + RED_BLOCKS + 128 doubles
   int* order = nullptr;      // q
   int* coff = nullptr;       // q + 1
   int* cidx = nullptr;       // q
@@ -23,15 +23,24 @@ struct EigScratch {
   GridBar* bar = nullptr;    // grid barrier of the cooperative Jacobi
   int* status = nullptr;     // device status word
   int num_sms = 0;
+  // optional phase profiling hooks of the caller: mark(mark_ctx, LYAP_PHASE_*) starts a
+  // timed phase; flops[LYAP_PHASE_*] accumulates algorithmic flops (host memory)
+  void (*mark)(void*, int) = nullptr;
+  void* mark_ctx = nullptr;
+  double* flops = nullptr;
 };
 
 // H (q x q, ldh, FP64, symmetric; not modified) = Q diag(w) Q^T, w ascending,
-// Q (q x q, ldq).  FP32 parallel cyclic Jacobi, then (refine != 0) FP64
+// Q (q x q, ldq).  FP32 Jacobi (two-sided in shared memory for q <= 160, block
+// one-sided on the shifted matrix H + 2 ||H||_F I across the GPU beyond), then (refine != 0) FP64
 // refinement: Ogita-Aishima steps, Newton-Schulz re-orthonormalisation, and
 // re-diagonalisation of every remaining eigenvalue cluster (its block of
 // X^T H X, shifted and scaled to unit size, by a batched FP32 Jacobi), repeated
 // until the coupling left is below 1e-15 ||H||_2.
 int sym_eig(const double* H, int64_t q, int64_t ldh, double* w, double* Q, int64_t ldq, int refine,
             EigScratch& sc, cudaStream_t s);
+
+// Floats of EigScratch::work32 that sym_eig needs for order q (block Jacobi for q > 160).
+size_t bjac_work_floats(int q);
 
 }  // namespace lyap

@@ -88,6 +88,7 @@ struct lyap_ctx {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<int> marks_phase;
   size_t marks_used = 0;
+  double flops[LYAP_NUM_PHASES] = {};  // algorithmic flops per phase (host-side count)
 };
 
 namespace lyap {
@@ -109,7 +110,10 @@ static void mark(Ctx& C, int phase) {
   C.marks_phase[C.marks_used] = phase;
   ++C.marks_used;
 }
+// mark() for the eigensolver (EigScratch::mark)
+static void mark_cb(void* ctx, int phase) { mark(*static_cast<Ctx*>(ctx), phase); }
 static void collect_marks(Ctx& C, lyap_info_t* info) {
+  for (int p = 0; p < LYAP_NUM_PHASES; ++p) info->phase_flops[p] += C.flops[p];
   if (!C.profile) return;
   mark(C, LYAP_PHASE_OTHER);
   cudaEventSynchronize(C.ev_pool[C.marks_used - 1]);
@@ -466,14 +470,14 @@ static int prepare_newton(Ctx& C, int n, int m, int prec) {
 
 static int prepare_eig(Ctx& C, int q) {
   const size_t qq = (size_t)q * q;
-  LYAP_TRY(ensure(C.eigWork32, 2 * qq * 4 + 64));
+  LYAP_TRY(ensure(C.eigWork32, std::max(2 * qq, bjac_work_floats(q)) * 4 + 64));
   LYAP_TRY(ensure(C.eigX, qq * 8 + 64));
   LYAP_TRY(ensure(C.eigR, qq * 8 + 64));
   LYAP_TRY(ensure(C.eigS, qq * 8 + 64));
   LYAP_TRY(ensure(C.eigHX, qq * 8 + 64));
   LYAP_TRY(ensure(C.eigE, qq * 8 + 64));
   LYAP_TRY(ensure(C.eigLam, (size_t)q * 8 + 64));
-  LYAP_TRY(ensure(C.eigRed, (size_t)(16 + RED_BLOCKS + 16) * 8));
+  LYAP_TRY(ensure(C.eigRed, (size_t)(16 + RED_BLOCKS + 128) * 8));
   LYAP_TRY(ensure(C.eigW, qq * 8 + 64));
   LYAP_TRY(ensure(C.eigPv, (size_t)2 * q * 8 + 64));
   LYAP_TRY(ensure(C.eigInt, (size_t)(3 * q + 16) * 4));
@@ -496,6 +500,9 @@ static int prepare_eig(Ctx& C, int q) {
   C.eig.bar = P<GridBar>(C.qrBar);
   C.eig.status = P<int>(C.qrStatus);
   C.eig.num_sms = C.num_sms;
+  C.eig.mark = mark_cb;
+  C.eig.mark_ctx = &C;
+  C.eig.flops = C.flops;
   return LYAP_OK;
 }
 
@@ -517,6 +524,7 @@ static int invert_current(Ctx& C, const T* Acur, int n, int prec) {
   iota_kernel<<<nblk(n), 256, 0, C.s>>>(W.perm[0], n);
   LYAP_CUDA_TRY(cudaGetLastError());
   lyap_count_launch();
+  C.flops[LYAP_PHASE_INVERT] += 2.0 * (double)n * n * n;
   return gj_invert_run(W, prec, C.s);
 }
 
@@ -1429,6 +1437,7 @@ static int solve_entry(lyap_ctx_t* C, const double* A, int64_t n, int64_t lda, c
   const int64_t l0 = g_launches;
   C->profile = opts->profile != 0;
   C->marks_used = 0;
+  for (double& f : C->flops) f = 0.0;
   cudaEventRecord(C->e0, C->s);
   mark(*C, LYAP_PHASE_OTHER);
   int st = solve_common(*C, pb, *opts, refine, Z, ldz, z_cap, D, rank_out, inf);

@@ -19,7 +19,9 @@ PREC = {"fp64": FP64, "fp32": FP32, "fp16": FP16, "bf16": BF16}
 SCALE_FROB, SCALE_DET, SCALE_NONE = 0, 1, 2
 SCALING = {"frob": SCALE_FROB, "det": SCALE_DET, "none": SCALE_NONE}
 
-PHASES = ["invert", "newton", "factor", "compress", "resfac", "eig", "solupt", "other"]
+PHASES = ["invert", "newton", "factor", "compress", "resfac", "eig", "solupt", "other", "eig_refine", "spare9",
+          "spare10", "spare11"]
+NUM_PHASES = 12
 
 OK = 0
 ERR_ARG, ERR_NONFINITE, ERR_SINGULAR, ERR_NOCONV, ERR_CAPACITY, ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM = (
@@ -43,13 +45,16 @@ class LyapInfo(C.Structure):
         ("newton_total", C.c_int), ("newton_max", C.c_int), ("n_inversions", C.c_int), ("stagnated", C.c_int),
         ("converged", C.c_int), ("n_res", C.c_int), ("res_final", C.c_double), ("res_hist", C.c_double * 64),
         ("mu", C.c_double * 64), ("kernel_launches", C.c_int64), ("device_ms", C.c_double),
-        ("phase_ms", C.c_double * 8), ("phase_calls", C.c_int64 * 8),
+        ("phase_ms", C.c_double * 12), ("phase_calls", C.c_int64 * 12), ("phase_flops", C.c_double * 12),
     ]
 
     def as_dict(self) -> dict:
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("res_hist", "mu", "phase_ms", "phase_calls")}
-        d["phase_ms"] = dict(zip(PHASES, list(self.phase_ms)))
-        d["phase_calls"] = dict(zip(PHASES, list(self.phase_calls)))
+        d = {f: getattr(self, f) for f, _ in self._fields_
+             if f not in ("res_hist", "mu", "phase_ms", "phase_calls", "phase_flops")}
+        used = [i for i, p in enumerate(PHASES) if not p.startswith("spare")]
+        d["phase_ms"] = {PHASES[i]: self.phase_ms[i] for i in used}
+        d["phase_calls"] = {PHASES[i]: self.phase_calls[i] for i in used}
+        d["phase_flops"] = {PHASES[i]: self.phase_flops[i] for i in used}
         d["res_hist"] = list(self.res_hist[: self.n_res])
         d["mu"] = [m for m in self.mu[: max(self.newton_max, 0)]]
         return d

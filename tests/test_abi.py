@@ -36,7 +36,7 @@ def test_struct_layout_matches_header():
     # sizes of the option / info structs as laid out by the C compiler
     from paper_2510_02126_gb300 import lyap as liblyap
     assert ctypes.sizeof(liblyap.LyapOpts) == 4 * 2 + 8 + 4 * 3 + 8 * 3 + 4 * 2 + 8 * 4 + 4 * 2 + 4 * 8 + 4
-    assert ctypes.sizeof(liblyap.LyapInfo) == 4 * 10 + 8 + 8 * 64 * 2 + 8 + 8 + 8 * 8 * 2
+    assert ctypes.sizeof(liblyap.LyapInfo) == 4 * 10 + 8 + 8 * 64 * 2 + 8 + 8 + 8 * 12 * 3
 
 
 def test_opts_default_without_gpu():
