@@ -164,6 +164,34 @@ int lyap_solve_ir(lyap_ctx_t* ctx, const double* A, int64_t n, int64_t lda,
                   double* D, int64_t* rank_out, lyap_info_t* info);
 
 /*
+ * Adjoint of the solve (no counterpart in the paper; it follows from differentiating
+ * Eq. (1.1)): gradients of the loss l = trace(C X C^T), X = Z diag(D) Z^T (D == NULL:
+ * X = Z Z^T), the solution of A X + X A^T + L S L^T = 0 (S == NULL: S = I).
+ * With Y solving the adjoint equation A^T Y + Y A + C^T C = 0,
+ *   dl/dA = 2 Y X (n x n),  dl/dL = 2 Y L S (n x m),  dl/dS = L^T Y L (m x m),  dl/dW = Y.
+ * Y = Zy Zy^T is computed by the mixed-precision refinement of lyap_solve_ir (precisions
+ * and tolerances from opts).  When the context still holds the inverse sequence of this
+ * A (the last lyap_solve_ir / lyap_sign_solve on it, same u_s, recognised by a device
+ * fingerprint of A), every Newton solve replays it transposed -- the sign-Newton
+ * sequence of A^T is (A_k^{-1})^T with the same mu_k -- and no inversion is computed
+ * (info->n_inversions = 0); otherwise the sequence of A^T is computed and stored.
+ *   A (n x n, lda), L (n x m, ldl), S (m x m, lds, or NULL), Z (n x r, ldz), D (r or NULL):
+ *              the forward problem and its solution factor, DEVICE, column-major FP64
+ *   Cm         q x n (ldc >= q), DEVICE: the loss matrix C
+ *   dA, dL, dS optional DEVICE outputs (NULL to skip), leading dimensions as named
+ *   Zy         optional DEVICE output n x zy_cap (ldzy): the adjoint factor; *rank_y its
+ *              column count (required with Zy; LYAP_ERR_CAPACITY if zy_cap is too small)
+ *   info       as for lyap_solve_ir, describing the adjoint refinement
+ * Returns as lyap_solve_ir (warnings > 0 still produce gradients from the best Zy).
+ */
+int lyap_adjoint(lyap_ctx_t* ctx, const double* A, int64_t n, int64_t lda,
+                 const double* L, int64_t ldl, int64_t m, const double* S, int64_t lds,
+                 const double* Z, int64_t ldz, int64_t r, const double* D,
+                 const double* Cm, int64_t ldc, int64_t q, const lyap_opts_t* opts,
+                 double* dA, int64_t ldda, double* dL, int64_t lddl, double* dS, int64_t ldds,
+                 double* Zy, int64_t ldzy, int64_t zy_cap, int64_t* rank_y, lyap_info_t* info);
+
+/*
  * Relative residual of Eq. (4.1),
  *   ||A X + X A^T + W||_F / (||W||_F + 2 ||X||_F ||A||_F),  X = Z Z^T or Z diag(D) Z^T,
  * evaluated in FP64 from the factors without forming n x n matrices (thin QR of

@@ -71,6 +71,7 @@ struct lyap_ctx {
   // stored inverse sequence (Sec. 3.4)
   lyap::Buf store, dmu, dex;
   int store_n = 0, store_prec = -1, store_count = 0, store_e0 = 0;
+  double store_fp = 0.0;   // fingerprint of the matrix whose inverse sequence is stored
   size_t store_elt = 0;
   int64_t store_ld = 0;    // row pitch (elements) of a stored inverse
   int64_t store_rows = 0;  // rows allocated per stored inverse
@@ -80,6 +81,8 @@ struct lyap_ctx {
   lyap::QRScratch qr;
   lyap::Buf qrBar, qrStatus, qrCand, qrNorms, qrPiv, qrRdiag, qrWork, qrRank;
   lyap::EigScratch eig;
+  // adjoint: A^T, C^T, the adjoint factor and the gradient products
+  lyap::Buf At, Ct, ZY, adjT;
   lyap::Buf eigWork32, eigX, eigR, eigS, eigHX, eigE, eigLam, eigRed, eigW, eigPv, eigInt;
   void* hpin = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -506,10 +509,102 @@ static int prepare_eig(Ctx& C, int q) {
   return LYAP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// adjoint support
+// ---------------------------------------------------------------------------
+// Partial sums of sum_ij a_ij w_ij with fixed pseudo-random weights in [1, 2): a
+// fingerprint that identifies the matrix whose inverse sequence is stored.
+__global__ void fingerprint_kernel(const double* __restrict__ A, int n, int64_t lda, double* __restrict__ part) {
+  __shared__ double red[32];
+  double t = 0.0;
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / n, i = e - j * n;
+    const uint32_t h = ((uint32_t)i * 2654435761u) ^ ((uint32_t)j * 40503u + 0x9e3779b9u);
+    t += A[i + j * lda] * (1.0 + (double)(h % 1009u) / 1009.0);
+  }
+  t = warp_sum(t);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double u = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) u += red[w];
+    part[blockIdx.x] = u;
+  }
+}
+__global__ void sum_parts_kernel(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double u = 0.0;
+    for (int b = 0; b < nb; ++b) u += part[b];  // fixed order: the same bits every call
+    *out = u;
+  }
+}
+// In-place transpose of `count` square n x n matrices (row pitch ld, slot stride) of
+// U-sized elements; 32 x 32 tiles, the tile pair (bi, bj), bi <= bj, per CTA.
+template <typename U>
+__global__ void transpose_slots_kernel(U* __restrict__ M, int n, int64_t ld, size_t slot) {
+  __shared__ U t1[32][33], t2[32][33];
+  const int bi = blockIdx.y, bj = blockIdx.x;
+  if (bi > bj) return;
+  U* Ms = M + (size_t)blockIdx.z * slot;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    const int i1 = bi * 32 + r, j1 = bj * 32 + tx;
+    if (i1 < n && j1 < n) t1[r][tx] = Ms[(int64_t)i1 * ld + j1];
+    const int i2 = bj * 32 + r, j2 = bi * 32 + tx;
+    if (bi != bj && i2 < n && j2 < n) t2[r][tx] = Ms[(int64_t)i2 * ld + j2];
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    // tile (bi, bj) <- transpose of tile (bj, bi); tile (bj, bi) <- transpose of tile (bi, bj)
+    const int i1 = bi * 32 + r, j1 = bj * 32 + tx;
+    if (i1 < n && j1 < n) Ms[(int64_t)i1 * ld + j1] = (bi != bj) ? t2[tx][r] : t1[tx][r];
+    const int i2 = bj * 32 + r, j2 = bi * 32 + tx;
+    if (bi != bj && i2 < n && j2 < n) Ms[(int64_t)i2 * ld + j2] = t1[tx][r];
+  }
+}
+// B (n x m, ld n) = A^T for A (m x n, lda), FP64 column-major
+__global__ void transpose64_kernel(const double* __restrict__ A, int m, int n, int64_t lda, double* __restrict__ B) {
+  __shared__ double t[32][33];
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;  // block of A: rows i0.., cols j0..
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int i = i0 + threadIdx.x, j = j0 + r;
+    if (i < m && j < n) t[r][threadIdx.x] = A[i + (int64_t)j * lda];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int j = j0 + threadIdx.x, i = i0 + r;  // B[j, i] = A[i, j]
+    if (i < m && j < n) B[j + (int64_t)i * n] = t[threadIdx.x][r];
+  }
+}
+
 static int sync_read(Ctx& C, const void* dev, void* host, size_t bytes) {
   LYAP_CUDA_TRY(cudaMemcpyAsync(C.hpin, dev, bytes, cudaMemcpyDeviceToHost, C.s));
   LYAP_CUDA_TRY(cudaStreamSynchronize(C.s));
   memcpy(host, C.hpin, bytes);
+  return LYAP_OK;
+}
+
+static int fingerprint(Ctx& C, const double* A, int n, int64_t lda, double* out) {
+  fingerprint_kernel<<<RED_BLOCKS, 256, 0, C.s>>>(A, n, lda, P<double>(C.part) + 5 * RED_BLOCKS);
+  sum_parts_kernel<<<1, 32, 0, C.s>>>(P<double>(C.part) + 5 * RED_BLOCKS, RED_BLOCKS, P<double>(C.scal) + 310);
+  LYAP_CUDA_TRY(cudaGetLastError());
+  lyap_count_launch(2);
+  return sync_read(C, P<double>(C.scal) + 310, out, sizeof(double));
+}
+
+// Transpose every stored inverse in place: A_k^{-1} -> A_k^{-T} (and back).
+static int transpose_store(Ctx& C) {
+  if (C.store_count == 0) return LYAP_OK;
+  const int n = C.store_n;
+  const unsigned nt = (unsigned)ceil_div(n, 32);
+  dim3 grid(nt, nt, (unsigned)C.store_count), block(32, 8);
+  const size_t slot = (size_t)C.store_rows * C.store_ld;
+  if (C.store_elt == 2) transpose_slots_kernel<uint16_t><<<grid, block, 0, C.s>>>((uint16_t*)C.store.p, n, C.store_ld, slot);
+  else if (C.store_elt == 4) transpose_slots_kernel<uint32_t><<<grid, block, 0, C.s>>>((uint32_t*)C.store.p, n, C.store_ld, slot);
+  else transpose_slots_kernel<uint64_t><<<grid, block, 0, C.s>>>((uint64_t*)C.store.p, n, C.store_ld, slot);
+  LYAP_CUDA_TRY(cudaGetLastError());
+  lyap_count_launch();
   return LYAP_OK;
 }
 
@@ -1006,6 +1101,7 @@ static int newton_solve(Ctx& C, const Problem& pb, const double* Lr, int mr, con
     frexp(sqrt(ssA), &e0);
     e0 -= 1;
     C.store_e0 = e0;
+    LYAP_TRY(fingerprint(C, pb.A, n, pb.lda, &C.store_fp));
     LYAP_TRY(cm64_to_rm<T>(pb.A, n, pb.lda, ldexp(1.0, -e0), P<T>(C.A0), C.s));
   } else if (C.store_n != n || C.store_prec != o.u_s || C.store_count == 0) {
     lyap_set_error_message("no stored inverse sequence for this problem", __FILE__, __LINE__);
@@ -1289,7 +1385,7 @@ static int check_inputs_finite(Ctx& C, const Problem& pb) {
 }
 
 static int solve_common(Ctx& C, const Problem& pb, const lyap_opts_t& o, bool refine, double* Z, int64_t ldz,
-                        int64_t z_cap, double* D, int64_t* rank_out, lyap_info_t* info) {
+                        int64_t z_cap, double* D, int64_t* rank_out, lyap_info_t* info, bool replay_first = false) {
   const int n = pb.n, m = pb.m;
   const bool ldlt = (pb.S != nullptr);
   LYAP_TRY(ensure(C.scal, 4096));
@@ -1304,14 +1400,14 @@ static int solve_common(Ctx& C, const Problem& pb, const lyap_opts_t& o, bool re
   LYAP_TRY(ensure(C.Zbest, (size_t)n * (zcap_ir) * 8));
   LYAP_TRY(ensure(C.ysol, (size_t)(zcap_ir) * 8));
   LYAP_TRY(ensure(C.ybest, (size_t)(zcap_ir) * 8));
-  // first solve (computes and stores the inverse sequence)
+  // first solve (computes and stores the inverse sequence, or replays a stored one)
   int c = 0, iters = 0;
-  LYAP_TRY(newton_solve_any(C, pb, Lw, m, sd, ldlt, o, true, P<double>(C.Zs), n, zcap_ir, P<double>(C.ysol), &c,
-                            info, &iters));
+  LYAP_TRY(newton_solve_any(C, pb, Lw, m, sd, ldlt, o, !replay_first, P<double>(C.Zs), n, zcap_ir,
+                            P<double>(C.ysol), &c, info, &iters));
   info->newton_calls = 1;
   info->newton_total = iters;
   info->newton_max = iters;
-  info->n_inversions = iters;
+  info->n_inversions = replay_first ? 0 : iters;
   // normalisation constants
   double* sc = P<double>(C.scal);
   {
@@ -1453,6 +1549,140 @@ static int solve_entry(lyap_ctx_t* C, const double* A, int64_t n, int64_t lda, c
   return st;
 }
 
+
+// Adjoint of the last solve (not in the paper): Y = Z_Y Z_Y^T solves A^T Y + Y A + C^T C = 0
+// by the same refinement, its Newton solves replaying the stored A_k^{-1} transposed (the
+// sign-Newton sequence of A^T is the transposed sequence of A with the same mu_k, since
+// the Frobenius norm and determinant are transpose-invariant); then
+// dl/dA = 2 Y X, dl/dL = 2 Y L S, dl/dS = L^T Y L for X = Z D Z^T.
+static int adjoint_entry(lyap_ctx_t* Cp, const double* A, int64_t n, int64_t lda, const double* L, int64_t ldl,
+                         int64_t m, const double* S, int64_t lds, const double* Z, int64_t ldz, int64_t r,
+                         const double* D, const double* Cm, int64_t ldc, int64_t q, const lyap_opts_t* opts,
+                         double* dA, int64_t ldda, double* dL, int64_t lddl, double* dS, int64_t ldds, double* Zy,
+                         int64_t ldzy, int64_t zy_cap, int64_t* rank_y, lyap_info_t* info) {
+  if (!Cp || !A || !L || !Z || !Cm || !opts || n <= 0 || m <= 0 || r < 0 || q <= 0) return LYAP_ERR_ARG;
+  if (lda < n || ldl < n || ldz < n || ldc < q || (S && lds < m)) return LYAP_ERR_ARG;
+  if ((dA && ldda < n) || (dL && lddl < n) || (dS && ldds < m) || (Zy && (ldzy < n || !rank_y))) return LYAP_ERR_ARG;
+  Ctx& C = *Cp;
+  const int ni = (int)n, mi = (int)m, qi = (int)q, ri = (int)r;
+  lyap_info_t local;
+  lyap_info_t* inf = info ? info : &local;
+  memset(inf, 0, sizeof(*inf));
+  const int64_t l0 = g_launches;
+  C.profile = opts->profile != 0;
+  C.marks_used = 0;
+  for (double& f : C.flops) f = 0.0;
+  cudaEventRecord(C.e0, C.s);
+  mark(C, LYAP_PHASE_OTHER);
+  int st = LYAP_OK;
+  bool transposed = false;
+  do {
+    LYAP_TRY(ensure(C.scal, 4096));
+    LYAP_TRY(ensure(C.part, (size_t)6 * RED_BLOCKS * 8));
+    LYAP_TRY(ensure(C.At, (size_t)n * n * 8));
+    LYAP_TRY(ensure(C.Ct, (size_t)n * q * 8));
+    const int64_t cap = n + 8;
+    LYAP_TRY(ensure(C.ZY, (size_t)n * cap * 8));
+    dim3 blk(32, 8);
+    transpose64_kernel<<<dim3((unsigned)ceil_div(n, 32), (unsigned)ceil_div(n, 32)), blk, 0, C.s>>>(A, ni, ni, lda,
+                                                                                                  P<double>(C.At));
+    transpose64_kernel<<<dim3((unsigned)ceil_div(n, 32), (unsigned)ceil_div(q, 32)), blk, 0, C.s>>>(Cm, qi, ni, ldc,
+                                                                                                  P<double>(C.Ct));
+    LYAP_CUDA_TRY(cudaGetLastError());
+    lyap_count_launch(2);
+    // C = 0: Y = 0 and every gradient vanishes
+    {
+      double cc = 0.0;
+      LYAP_TRY(sumsq<double>(P<double>(C.Ct), n, q, n, P<double>(C.scal) + 312, P<double>(C.part), C.s));
+      LYAP_TRY(sync_read(C, P<double>(C.scal) + 312, &cc, sizeof(double)));
+      if (cc == 0.0) {
+        if (dL) LYAP_TRY(set_zero<double>(dL, n, m, lddl, C.s));
+        if (dS) LYAP_TRY(set_zero<double>(dS, m, m, ldds, C.s));
+        if (dA) LYAP_TRY(set_zero<double>(dA, n, n, ldda, C.s));
+        if (rank_y) *rank_y = 0;
+        inf->converged = 1;
+        break;
+      }
+    }
+    // replay the forward inverse sequence if it belongs to this A, else build one for A^T
+    double fp = 0.0;
+    LYAP_TRY(fingerprint(C, A, ni, lda, &fp));
+    const bool replay = C.store_count > 0 && C.store_n == ni && C.store_prec == opts->u_s && fp == C.store_fp;
+    if (replay) {
+      LYAP_TRY(transpose_store(C));
+      transposed = true;
+    }
+    Problem pbY{P<double>(C.At), ni, n, P<double>(C.Ct), n, qi, nullptr, 0};
+    int64_t ry = 0;
+    st = solve_common(C, pbY, *opts, true, P<double>(C.ZY), n, cap, nullptr, &ry, inf, replay);
+    if (st < 0) break;
+    if (transposed) {
+      LYAP_TRY(transpose_store(C));
+      transposed = false;
+    }
+    if (rank_y) *rank_y = ry;
+    if (Zy) {
+      if (ry > zy_cap) {
+        lyap_set_error_message("adjoint factor capacity too small", __FILE__, __LINE__);
+        st = LYAP_ERR_CAPACITY;
+        break;
+      }
+      LYAP_TRY((copy_cast<double, double>(P<double>(C.ZY), n, ry, n, Zy, ldzy, 1.0, C.s)));
+    }
+    // gradient products (FP64)
+    const int ryi = (int)ry;
+    LYAP_TRY(ensure(C.adjT, (size_t)(std::max(ryi, 1) * (mi + ri) + n * (mi + ri) + 64) * 8));
+    double* T1 = P<double>(C.adjT);                               // Z_Y^T L      (ry x m)
+    double* T2 = T1 + (size_t)std::max(ryi, 1) * mi;              // Z_Y T1       (n x m)
+    double* T3 = T2 + (size_t)n * mi;                             // Z_Y^T Z      (ry x r)
+    double* T4 = T3 + (size_t)std::max(ryi, 1) * std::max(ri, 1); // Z_Y T3 D     (n x r)
+    const double* Yf = P<double>(C.ZY);
+    if (ryi == 0) {
+      if (dL) LYAP_TRY(set_zero<double>(dL, n, m, lddl, C.s));
+      if (dS) LYAP_TRY(set_zero<double>(dS, m, m, ldds, C.s));
+      if (dA) LYAP_TRY(set_zero<double>(dA, n, n, ldda, C.s));
+      break;
+    }
+    LYAP_TRY(gemm<double>('T', 'N', ryi, mi, ni, 1.0, Yf, n, L, ldl, 0.0, T1, ryi, C.s));
+    if (dL) {
+      if (S) {
+        LYAP_TRY(gemm<double>('N', 'N', ni, mi, ryi, 1.0, Yf, n, T1, ryi, 0.0, T2, n, C.s));
+        LYAP_TRY(gemm<double>('N', 'N', ni, mi, mi, 2.0, T2, n, S, lds, 0.0, dL, lddl, C.s));
+      } else {
+        LYAP_TRY(gemm<double>('N', 'N', ni, mi, ryi, 2.0, Yf, n, T1, ryi, 0.0, dL, lddl, C.s));
+      }
+    }
+    if (dS) LYAP_TRY(gemm<double>('T', 'N', mi, mi, ryi, 1.0, T1, ryi, T1, ryi, 0.0, dS, ldds, C.s));
+    if (dA) {
+      if (ri == 0) {
+        LYAP_TRY(set_zero<double>(dA, n, n, ldda, C.s));
+      } else {
+        LYAP_TRY(gemm<double>('T', 'N', ryi, ri, ni, 1.0, Yf, n, Z, ldz, 0.0, T3, ryi, C.s));
+        LYAP_TRY(gemm<double>('N', 'N', ni, ri, ryi, 1.0, Yf, n, T3, ryi, 0.0, T4, n, C.s));
+        if (D) {
+          scale_cols_dev_kernel<<<nblk((int64_t)n * r), 256, 0, C.s>>>(T4, ni, ri, ri + 1, D, T4);
+          LYAP_CUDA_TRY(cudaGetLastError());
+          lyap_count_launch();
+        }
+        LYAP_TRY(gemm<double>('N', 'T', ni, ni, ri, 2.0, T4, n, Z, ldz, 0.0, dA, ldda, C.s));
+      }
+    }
+  } while (false);
+  if (transposed) {
+    const int t = transpose_store(C);
+    if (st >= 0 && t < 0) st = t;
+  }
+  collect_marks(C, inf);
+  C.profile = false;
+  cudaEventRecord(C.e1, C.s);
+  cudaEventSynchronize(C.e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, C.e0, C.e1);
+  inf->device_ms = ms;
+  inf->kernel_launches = g_launches - l0;
+  inf->status = st;
+  return st;
+}
 }  // namespace lyap
 
 extern "C" {
@@ -1467,6 +1697,15 @@ int lyap_solve_ir(lyap_ctx_t* C, const double* A, int64_t n, int64_t lda, const 
                   const double* S, int64_t lds, const lyap_opts_t* opts, double* Z, int64_t ldz, int64_t z_cap,
                   double* D, int64_t* rank_out, lyap_info_t* info) {
   return solve_entry(C, A, n, lda, L, ldl, m, S, lds, opts, Z, ldz, z_cap, D, rank_out, info, true);
+}
+
+int lyap_adjoint(lyap_ctx_t* C, const double* A, int64_t n, int64_t lda, const double* L, int64_t ldl, int64_t m,
+                 const double* S, int64_t lds, const double* Z, int64_t ldz, int64_t r, const double* D,
+                 const double* Cm, int64_t ldc, int64_t q, const lyap_opts_t* opts, double* dA, int64_t ldda,
+                 double* dL, int64_t lddl, double* dS, int64_t ldds, double* Zy, int64_t ldzy, int64_t zy_cap,
+                 int64_t* rank_y, lyap_info_t* info) {
+  return adjoint_entry(C, A, n, lda, L, ldl, m, S, lds, Z, ldz, r, D, Cm, ldc, q, opts, dA, ldda, dL, lddl, dS, ldds,
+                       Zy, ldzy, zy_cap, rank_y, info);
 }
 
 int lyap_residual(lyap_ctx_t* C, const double* A, int64_t n, int64_t lda, const double* L, int64_t ldl, int64_t m,

@@ -84,6 +84,9 @@ SIGNATURES = {
                                 C.POINTER(_D)]),
     "lyap_invert": (C.c_int, [_P, _P, _I64, _I64, C.c_int, _P, _I64, _P, C.POINTER(_D)]),
     "lyap_invert_noalloc": (C.c_int, [_P, _I64, _I64, C.c_int, _P, _I64, _P, C.POINTER(_D), _P]),
+    "lyap_adjoint": (C.c_int, [_P, _P, _I64, _I64, _P, _I64, _I64, _P, _I64, _P, _I64, _I64, _P, _P, _I64, _I64,
+                               C.POINTER(LyapOpts), _P, _I64, _P, _I64, _P, _I64, _P, _I64, _I64, C.POINTER(_I64),
+                               C.POINTER(LyapInfo)]),
     "lyap_rank_trunc": (C.c_int, [_P, _P, _I64, _I64, _I64, _D, C.POINTER(_I64)]),
     "lyap_sym_eig": (C.c_int, [_P, _P, _I64, _I64, _P, _P, _I64, C.c_int]),
     "lyap_last_error": (C.c_char_p, []),
@@ -229,6 +232,68 @@ def sign_solve(A, L, S=None, z_cap=None, opts=None, **kw):
     return _solve("lyap_sign_solve", A, L, S, z_cap, opts if opts is not None else make_opts(**kw))
 
 
+def adjoint(A, L, Z, Cm, S=None, D=None, opts=None, want=("dA", "dL", "dS"), factor=False, **kw):
+    """Gradients of l = trace(C X C^T), X = Z diag(D) Z^T solving A X + X A^T + L S L^T = 0,
+    through lyap_adjoint (adjoint equation A^T Y + Y A + C^T C = 0 solved by the refinement,
+    replaying the context's stored inverse sequence transposed when it belongs to this A).
+    Returns dict(dA, dL, dS, Zy, info) (entries not requested are None)."""
+    ctx = context()
+    A, L, Z, Cm = _cm(A), _cm(L), _cm(Z), _cm(Cm)
+    n, m = L.shape
+    r = Z.shape[1]
+    q = Cm.shape[0]
+    Sd = _cm(S) if S is not None else None
+    Dd = D.contiguous() if D is not None else None
+    dev = A.device
+    dA = cm_empty(n, n, dev) if "dA" in want else None
+    dL = cm_empty(n, m, dev) if "dL" in want else None
+    dS = cm_empty(m, m, dev) if ("dS" in want and S is not None) else None
+    cap = n + 8
+    Zy = cm_empty(n, cap, dev) if factor else None
+    ry = _I64(0)
+    info = LyapInfo()
+    o = opts if opts is not None else make_opts(**kw)
+    ptr = lambda t: _P(t.data_ptr()) if t is not None else None  # noqa: E731
+    st = ctx.lib.lyap_adjoint(ctx.h, ptr(A), n, n, ptr(L), n, m, ptr(Sd), m, ptr(Z), n, r, ptr(Dd), ptr(Cm), q, q,
+                              C.byref(o), ptr(dA), n, ptr(dL), n, ptr(dS), m, ptr(Zy), n, cap, C.byref(ry),
+                              C.byref(info))
+    _check(st)
+    return {"dA": dA, "dL": dL, "dS": dS, "Zy": Zy[:, : ry.value] if Zy is not None else None, "info": info}
+
+
+class LyapTraceLoss(torch.autograd.Function):
+    """l = trace(C X C^T) for the solution X = Z diag(D) Z^T of A X + X A^T + L S L^T = 0
+    (lyap_solve_ir forward; S = None: W = L L^T).  backward: dA, dL, dS from lyap_adjoint
+    (which replays the forward inverse sequence transposed), dC = 2 C X."""
+
+    @staticmethod
+    def forward(fctx, A, L, Cm, S=None, opts=None):
+        Z, D, info = solve_ir(A, L, S, opts=opts)
+        CZ = Cm @ Z
+        loss = (CZ * CZ * D[None, :]).sum() if D is not None else (CZ * CZ).sum()
+        fctx.opts = opts
+        fctx.info = info
+        fctx.save_for_backward(A, L, Cm, S if S is not None else torch.empty(0, device=A.device), Z,
+                               D if D is not None else torch.empty(0, device=A.device))
+        return loss
+
+    @staticmethod
+    def backward(fctx, g):
+        A, L, Cm, S, Z, D = fctx.saved_tensors
+        S = S if S.numel() else None
+        D = D if D.numel() else None
+        out = adjoint(A, L, Z, Cm, S=S, D=D, opts=fctx.opts)
+        ZD = Z * D[None, :] if D is not None else Z
+        dC = 2.0 * (Cm @ ZD) @ Z.T
+        dS = g * out["dS"] if S is not None else None
+        return g * out["dA"], g * out["dL"], g * dC, dS, None
+
+
+def trace_loss(A, L, Cm, S=None, opts=None, **kw):
+    """Differentiable l = trace(C X C^T) (LyapTraceLoss)."""
+    return LyapTraceLoss.apply(A, L, Cm, S, opts if opts is not None else make_opts(**kw))
+
+
 def residual(A, L, Z, S=None, D=None) -> float:
     """Relative residual of Eq. (4.1) computed in FP64 on the GPU from the factors."""
     ctx = context()
@@ -309,5 +374,6 @@ lyap_sign_solve = sign_solve
 lyap_residual = residual
 lyap_invert = invert
 lyap_invert_noalloc = invert_noalloc
+lyap_adjoint = adjoint
 lyap_rank_trunc = rank_trunc
 lyap_sym_eig = sym_eig
