@@ -329,16 +329,18 @@ gj_update_simt(int n, int k, int bb, const T* __restrict__ Mcur, T* __restrict__
 }
 
 // Panel geometry (lane = column, NW warps x RPT rows per CTA, C = ceil(n / (NW RPT))
-// CTAs in one cluster, at most 16).  FP32: 16 warps x 32 rows per CTA (128 registers a
-// thread, 32 of them the panel).  FP64 (two registers per value, and FP64
+// CTAs in one cluster, at most 16).  FP32: 16 warps x 4, 8, 16 or 32 rows per CTA, about
+// 8 CTAs per cluster.  FP64 (two registers per value, and FP64
 // arithmetic slow enough that it must spread over many SMs): 16 warps x 4, 8 or 16 rows,
 // the smallest that fits n in 16 CTAs.
 struct PanelGeom { int nw, rpt, C; };
 static PanelGeom panel_geom(int n, int elt) {
   PanelGeom g;
   if (elt == 4) {
+    // about 8 CTAs per cluster: the per-column work shrinks with the rows a warp holds,
+    // while barriers of larger clusters cost more (measured at n = 1024 and 2048)
     g.nw = 16;
-    g.rpt = 32;
+    g.rpt = (n <= 512) ? 4 : (n <= 1024) ? 8 : (n <= 2048) ? 16 : 32;
   } else {
     g.nw = 16;
     g.rpt = (n <= 16 * 16 * 4) ? 4 : (n <= 16 * 16 * 8) ? 8 : 16;
@@ -395,6 +397,9 @@ template <typename T, typename OP>
 static int panel_dispatch(GJWork& W, int k, int step, cudaStream_t s) {
   const PanelGeom g = panel_geom(W.n, sizeof(T));
   if constexpr (sizeof(T) == 4) {
+    if (g.rpt == 4) return panel_dispatch_g<T, 16, 4, OP>(W, k, step, s);
+    if (g.rpt == 8) return panel_dispatch_g<T, 16, 8, OP>(W, k, step, s);
+    if (g.rpt == 16) return panel_dispatch_g<T, 16, 16, OP>(W, k, step, s);
     return panel_dispatch_g<T, 16, 32, OP>(W, k, step, s);
   } else {
     if (g.rpt == 4) return panel_dispatch_g<T, 16, 4, OP>(W, k, step, s);

@@ -285,10 +285,204 @@ qrcp_kernel(T* __restrict__ Z, int64_t n, int64_t c, int64_t ldz, double tol, T*
   if (b == 0 && threadIdx.x == 0) *rank_out = (int)r;
 }
 
+// ---------------------------------------------------------------------------
+// The same QR with column pivoting with M = Z^T resident in the distributed shared
+// memory of one thread-block cluster: CTA `rank` owns columns [rank nc, rank nc + nc).
+// Columns are never swapped: each records the step at which it became the pivot, and
+// the output is assembled from that at the end.  Every CTA forms the reflector itself
+// from the pivot column (read from its owner through DSMEM), so a step takes a single
+// cluster barrier (after the candidates of the step are published; the candidate
+// slots are double-buffered by step parity).
+// ---------------------------------------------------------------------------
+// odd column pitch: threads walking different columns of the same row hit distinct banks
+__host__ __device__ inline int64_t qrcp_cluster_ld(int64_t c) { return c | 1; }
+template <typename T>
+__host__ __device__ inline size_t qrcp_cluster_smem(int64_t c, int64_t nc) {
+  return sizeof(T) * ((size_t)qrcp_cluster_ld(c) * nc + 3 * (size_t)nc + (size_t)c) + sizeof(int) * (size_t)nc + 64;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 1)
+qrcp_cluster_kernel(T* __restrict__ Z, int n, int c, int64_t ldz, int nc, double tol, int* __restrict__ rank_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ldm = (int)qrcp_cluster_ld(c);
+  T* Ms = reinterpret_cast<T*>(smem_raw);  // c x nc, column-major (ld = ldm)
+  T* nrm = Ms + (size_t)ldm * nc;
+  T* nref = nrm + nc;
+  T* bdg = nref + nc;                      // beta of a column chosen as pivot
+  T* v = bdg + nc;                         // the step's reflector (length c)
+  int* stepof = reinterpret_cast<int*>(v + c);  // step at which the column was chosen, -1 if not
+  __shared__ double slot_v[2], slot_t[2];
+  __shared__ int slot_i[2];
+  __shared__ double redd[8], redt[8];
+  __shared__ int redi[8];
+  __shared__ T red[32];
+  const int rk = (int)cluster_ctarank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int col0 = rk * nc;
+  const int ncl = max(0, min(nc, n - col0));
+  for (int e = tid; e < c * ncl; e += blockDim.x) {
+    const int l = e / ncl, i = e - l * ncl;
+    Ms[l + (size_t)i * ldm] = Z[col0 + i + l * ldz];
+  }
+  __syncthreads();
+  for (int i = tid; i < ncl; i += blockDim.x) {
+    T acc = T(0);
+    for (int l = 0; l < c; ++l) acc = fma(Ms[l + (size_t)i * ldm], Ms[l + (size_t)i * ldm], acc);
+    nrm[i] = acc;
+    nref[i] = acc;
+    stepof[i] = -1;
+  }
+  __syncthreads();
+  const int kmax = min(c, n);
+  int r = kmax;
+  double r11 = 0.0;
+  for (int j = 0; j < kmax; ++j) {
+    const int par = j & 1;
+    // (1) local candidate: largest remaining norm (lowest index on ties) and tail sum
+    double bv = -1.0, ts = 0.0;
+    int bi = -1;
+    for (int i = tid; i < ncl; i += blockDim.x) {
+      if (stepof[i] >= 0) continue;
+      const double w = (double)nrm[i];
+      ts += w;
+      if (bi < 0 || w > bv) { bv = w; bi = col0 + i; }
+    }
+    warp_argmax(bv, bi);
+    ts = warp_sum(ts);
+    if (lane == 0) { redd[warp] = bv; redi[warp] = bi; redt[warp] = ts; }
+    __syncthreads();
+    if (warp == 0) {
+      double v2 = (lane < nw) ? redd[lane] : -1.0;
+      int i2 = (lane < nw) ? redi[lane] : -1;
+      double t2 = (lane < nw) ? redt[lane] : 0.0;
+      warp_argmax(v2, i2);
+      t2 = warp_sum(t2);
+      if (lane == 0) { slot_v[par] = v2; slot_i[par] = i2; slot_t[par] = t2; }
+    }
+    cluster_sync_all();
+    // (2) pivot and truncation test (every CTA alike)
+    double pv = -1.0, tail = 0.0;
+    int p = -1;
+    if (lane < (int)gridDim.x) {
+      pv = dsmem_ld_f64(dsmem_map(&slot_v[par], lane));
+      p = dsmem_ld_s32(dsmem_map(&slot_i[par], lane));
+      tail = dsmem_ld_f64(dsmem_map(&slot_t[par], lane));
+    }
+    warp_argmax(pv, p);
+    tail = warp_sum(tail);
+    if (j == 0 && !(tail > 0.0)) { r = 0; break; }
+    if (j >= 1 && sqrt(fmax(tail, 0.0)) <= tol * r11) { r = j; break; }
+    // (3) reflector from rows j.. of the pivot column
+    const int po = p / nc, pl = p - po * nc;
+    for (int l = tid; l < c - j; l += blockDim.x) v[l] = dsmem_ld<T>(dsmem_map(&Ms[j + l + (size_t)pl * ldm], po));
+    __syncthreads();
+    T sig = T(0);
+    for (int l = 1 + tid; l < c - j; l += blockDim.x) sig = fma(v[l], v[l], sig);
+    sig = block_sum(sig, red);
+    const T alpha = v[0];
+    T beta, tj, scale;
+    if (sig == T(0)) { beta = alpha; tj = T(0); scale = T(0); }
+    else {
+      const T nrmx = sqrt(alpha * alpha + sig);
+      beta = (alpha <= T(0)) ? nrmx : -nrmx;
+      tj = (beta - alpha) / beta;
+      scale = T(1) / (alpha - beta);
+    }
+    __syncthreads();
+    for (int l = 1 + tid; l < c - j; l += blockDim.x) v[l] *= scale;
+    if (tid == 0) {
+      v[0] = T(1);
+      if (rk == po) { stepof[pl] = j; bdg[pl] = beta; }
+    }
+    if (j == 0) r11 = fabs((double)beta);
+    __syncthreads();
+    // (4) apply to the remaining owned columns (two threads per column, rows split by
+    //     parity, combined by one shuffle) + norm downdate
+    for (int t0 = 0; t0 < 2 * ncl; t0 += blockDim.x) {  // warp-uniform trip count (shuffles below)
+      const int t = t0 + tid;
+      const int i = min(t >> 1, ncl - 1), h = t & 1;
+      const bool live = (t < 2 * ncl) && stepof[i] < 0;
+      T* y = Ms + j + (size_t)i * ldm;
+      T w = T(0);
+      if (live)
+        for (int l = 1 + h; l < c - j; l += 2) w = fma(v[l], y[l], w);
+      w += __shfl_xor_sync(0xffffffffu, w, 1);
+      const T y0 = live ? y[0] : T(0);
+      w = (w + y0) * tj;
+      const T top = y0 - w;
+      T tail2 = T(0);
+      if (live)
+        for (int l = 1 + h; l < c - j; l += 2) {
+          const T nv = fma(-w, v[l], y[l]);
+          y[l] = nv;
+          tail2 = fma(nv, nv, tail2);
+        }
+      tail2 += __shfl_xor_sync(0xffffffffu, tail2, 1);
+      if (live && h == 0) {
+        y[0] = top;
+        T nn = nrm[i] - top * top;
+        const T eps = (sizeof(T) == 8) ? T(1.5e-8) : T(3.5e-4);
+        if (!(nn > eps * nref[i])) {
+          nn = tail2;
+          nref[i] = nn;
+        }
+        nrm[i] = (nn > T(0)) ? nn : T(0);
+      }
+    }
+    __syncthreads();
+  }
+  cluster_sync_all();  // keep this CTA's columns readable until every CTA is done
+  // (5) output rows l < r of R in original column order: Z[o, l] = R[l, position of o]
+  for (int e = tid; e < r * ncl; e += blockDim.x) {
+    const int l = e / ncl, i = e - l * ncl;
+    const int st = stepof[i];
+    T val;
+    if (st < 0 || l < st) val = Ms[l + (size_t)i * ldm];
+    else if (l == st) val = bdg[i];
+    else val = T(0);
+    Z[col0 + i + l * ldz] = val;
+  }
+  if (rk == 0 && tid == 0) *rank_out = r;
+}
+
+// Cluster size for the resident variant, or 0 when M = Z^T does not fit.
+template <typename T>
+static int qrcp_cluster_size(int64_t n, int64_t c) {
+  for (int C : {8, 16}) {
+    const int64_t nc = ceil_div(n, C);
+    if (qrcp_cluster_smem<T>(c, nc) <= (size_t)200 * 1024) return C;
+  }
+  return 0;
+}
+
 template <typename T>
 int qrcp_truncate(T* Z, int64_t n, int64_t c, int64_t ldz, double tol, QRScratch& sc, cudaStream_t s) {
   if (n <= 0 || c <= 0) {
     LYAP_CUDA_TRY(cudaMemsetAsync(sc.rank, 0, sizeof(int), s));
+    return LYAP_OK;
+  }
+  const int CL = (n >= 64) ? qrcp_cluster_size<T>(n, c) : 0;
+  if (CL > 0) {
+    const int nc = (int)ceil_div(n, CL);
+    const size_t smem = qrcp_cluster_smem<T>(c, nc);
+    auto kc = qrcp_cluster_kernel<T>;
+    LYAP_CUDA_TRY(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (CL > 8) LYAP_CUDA_TRY(cudaFuncSetAttribute(kc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    LYAP_CUDA_TRY(cudaLaunchKernelEx(&cfg, kc, Z, (int)n, (int)c, ldz, nc, tol, sc.rank));
+    lyap_count_launch();
     return LYAP_OK;
   }
   int G = (int)std::min<int64_t>(ceil_div(n, 8), sc.num_sms);
