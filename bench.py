@@ -318,7 +318,10 @@ def run_case(args):
     eig:<q>             two lyap_sym_eig calls (FP64-refined) on a seeded indefinite core
                         H = T P T^T (T upper triangular, P = diag(+-1)), the shape of the
                         residual cores of the refinement
-    solve:<u_s>         one lyap_solve_ir of the benchmark workload"""
+    solve:<u_s>         one lyap_solve_ir of the benchmark workload
+    batched:<count>     <count> random stable equations, n log-uniform in [64, 1024], rank 1..8,
+                        FP16-inner IR to 1e-12: lyap_solve_ir_batched against looped lyap_solve_ir
+                        (host wall clock; prints one JSON line)"""
     import numpy as np
     import torch
     from paper_2510_02126_gb300 import lyap
@@ -341,6 +344,39 @@ def run_case(args):
         d = make_problem()
         lyap.solve_ir(torch.tensor(d["A"], device=dev), torch.tensor(d["L"], device=dev), u_s=rest[0], tau_ir=TAU,
                       imax=10)
+    elif kind == "batched":
+        import time
+        import lyapgen
+        count = int(rest[0]) if rest else 256
+        eqs = lyapgen.batch_uneven(count=count, nmin=64, nmax=1024, rmax=8)
+        As = [torch.tensor(e["A"], device=dev) for e in eqs]
+        Ls = [torch.tensor(e["L"], device=dev) for e in eqs]
+        o = lyap.make_opts(u_s="fp16", tau_ir=TAU, imax=10)
+        lyap.solve_ir_batched(As[:4], Ls[:4], opts=o, raise_on_error=False)  # warm-up (pool, code paths)
+        for a, l in zip(As[:2], Ls[:2]):
+            lyap.solve_ir(a, l, opts=o)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Zs, infos, st = lyap.solve_ir_batched(As, Ls, opts=o, workers=8, raise_on_error=False)
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        infos1 = []
+        for a, l in zip(As, Ls):
+            try:
+                infos1.append(lyap.solve_ir(a, l, opts=o)[2])
+            except lyap.LyapError:
+                infos1.append(None)
+        torch.cuda.synchronize()
+        tl = time.perf_counter() - t0
+        ns = [e["A"].shape[0] for e in eqs]
+        print(json.dumps({"case": "batched", "count": count, "n_range": [min(ns), max(ns)], "status": st,
+                          "converged": sum(int(i.converged) for i in infos),
+                          "max_res": max(i.res_final for i in infos),
+                          "batched_solves_per_s": count / tb, "looped_solves_per_s": count / tl,
+                          "speedup": tl / tb, "workers": 8,
+                          "looped_converged": sum(int(i.converged) for i in infos1 if i is not None)}))
+        return 0
     else:
         raise SystemExit(f"unknown case {args.case}")
     torch.cuda.synchronize()

@@ -164,6 +164,25 @@ int lyap_solve_ir(lyap_ctx_t* ctx, const double* A, int64_t n, int64_t lda,
                   double* D, int64_t* rank_out, lyap_info_t* info);
 
 /*
+ * Many independent Cholesky-type refinements (Algorithm IR-Chol) in one call, for
+ * batches of small equations A_e X_e + X_e A_e^T + L_e L_e^T = 0 of uneven order: the
+ * equations run concurrently on `workers` internal contexts (each with its own
+ * non-blocking stream and host thread; <= 0 selects 8), largest n first.  Each equation
+ * is solved exactly as by lyap_solve_ir with the same opts.
+ *   A, L, Z    HOST arrays of nb DEVICE pointers: A[e] (n[e] x n[e]), L[e] (n[e] x m[e]),
+ *              Z[e] (n[e] x z_cap[e]); leading dimensions equal n[e]; column-major FP64
+ *   n, m, z_cap HOST arrays of nb sizes;  rank_out HOST array of nb ranks
+ *   info       optional HOST array of nb lyap_info_t, or NULL
+ * The call waits for the context stream first (inputs ready) and returns after every
+ * solve has finished.  Returns LYAP_OK, the first negative status of any equation (the
+ * others are still solved; lyap_last_error names the equation), or else the first warning.
+ */
+int lyap_solve_ir_batched(lyap_ctx_t* ctx, int nb, const double* const* A, const int64_t* n,
+                          const double* const* L, const int64_t* m, const lyap_opts_t* opts,
+                          double* const* Z, const int64_t* z_cap, int64_t* rank_out,
+                          lyap_info_t* info, int workers);
+
+/*
  * Adjoint of the solve (no counterpart in the paper; it follows from differentiating
  * Eq. (1.1)): gradients of the loss l = trace(C X C^T), X = Z diag(D) Z^T (D == NULL:
  * X = Z Z^T), the solution of A X + X A^T + L S L^T = 0 (S == NULL: S = I).
@@ -254,7 +273,7 @@ int lyap_rank_trunc(lyap_ctx_t* ctx, double* Z, int64_t n, int64_t c, int64_t ld
 int lyap_sym_eig(lyap_ctx_t* ctx, double* H, int64_t q, int64_t ldh, double* w, double* Q,
                  int64_t ldq, int fp64_refine);
 
-/* Message of the last error raised in this process (static storage). */
+/* Message of the last error raised on the calling host thread (thread-local storage). */
 const char* lyap_last_error(void);
 /* Human-readable name of a status code. */
 const char* lyap_status_string(int status);

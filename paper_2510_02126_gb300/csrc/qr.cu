@@ -4,6 +4,8 @@
 // FP64 arithmetic of the trailing updates runs on many SMs at once.
 #include "qr.cuh"
 
+#include <atomic>
+
 namespace lyap {
 
 template <typename T>
@@ -446,12 +448,14 @@ qrcp_cluster_kernel(T* __restrict__ Z, int n, int c, int64_t ldz, int nc, double
   if (rk == 0 && tid == 0) *rank_out = r;
 }
 
+constexpr size_t QRCP_CLUSTER_SMEM = 200 * 1024;  // dynamic shared memory cap per CTA
+
 // Cluster size for the resident variant, or 0 when M = Z^T does not fit.
 template <typename T>
 static int qrcp_cluster_size(int64_t n, int64_t c) {
   for (int C : {8, 16}) {
     const int64_t nc = ceil_div(n, C);
-    if (qrcp_cluster_smem<T>(c, nc) <= (size_t)200 * 1024) return C;
+    if (qrcp_cluster_smem<T>(c, nc) <= QRCP_CLUSTER_SMEM) return C;
   }
   return 0;
 }
@@ -467,8 +471,14 @@ int qrcp_truncate(T* Z, int64_t n, int64_t c, int64_t ldz, double tol, QRScratch
     const int nc = (int)ceil_div(n, CL);
     const size_t smem = qrcp_cluster_smem<T>(c, nc);
     auto kc = qrcp_cluster_kernel<T>;
-    LYAP_CUDA_TRY(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    if (CL > 8) LYAP_CUDA_TRY(cudaFuncSetAttribute(kc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    // attributes are set once, to their largest value: concurrent callers (batched
+    // solves) must never lower them between another caller's set and launch
+    static std::atomic<bool> attr_c{false};
+    if (!attr_c.load()) {
+      LYAP_CUDA_TRY(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)QRCP_CLUSTER_SMEM));
+      LYAP_CUDA_TRY(cudaFuncSetAttribute(kc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+      attr_c.store(true);
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(CL);
     cfg.blockDim = dim3(256);
@@ -490,7 +500,15 @@ int qrcp_truncate(T* Z, int64_t n, int64_t c, int64_t ldz, double tol, QRScratch
   if (G < 1) G = 1;
   const size_t smem = sizeof(T) * (size_t)c;
   auto kern = qrcp_kernel<T>;
-  if (smem > 48 * 1024) LYAP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (smem > QRCP_CLUSTER_SMEM) {
+    lyap_set_error_message("QR with column pivoting: factor too wide", __FILE__, __LINE__);
+    return LYAP_ERR_ARG;
+  }
+  static std::atomic<bool> attr_g{false};
+  if (smem > 48 * 1024 && !attr_g.load()) {
+    LYAP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)QRCP_CLUSTER_SMEM));
+    attr_g.store(true);
+  }
   LYAP_CUDA_TRY(cudaMemsetAsync(sc.bar, 0, sizeof(GridBar), s));
   T* M = (T*)sc.work;
   T* nrm = (T*)sc.norms;

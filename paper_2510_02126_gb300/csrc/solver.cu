@@ -2,7 +2,12 @@
 // mixed-precision iterative refinement (Sec. 2) on one GPU.  Every arithmetic
 // step runs in this library's kernels; the host only sequences launches and
 // reads back the device-computed scalars that steer the loops.
+#include <algorithm>
+#include <atomic>
 #include <cstdio>
+#include <mutex>
+#include <string>
+#include <thread>
 #include <cstring>
 #include <vector>
 
@@ -15,8 +20,10 @@
 // ---------------------------------------------------------------------------
 // process-wide diagnostics
 // ---------------------------------------------------------------------------
-static char g_err[512] = "";
-static int64_t g_launches = 0;
+// last error message and kernel-launch count of the calling host thread (a call runs on
+// one thread; batched solves run their equations on worker threads)
+static thread_local char g_err[512] = "";
+static thread_local int64_t g_launches = 0;
 
 void lyap_set_error_message(const char* what, const char* file, int line) {
   snprintf(g_err, sizeof(g_err), "%s (%s:%d)", what, file, line);
@@ -92,6 +99,9 @@ struct lyap_ctx {
   std::vector<int> marks_phase;
   size_t marks_used = 0;
   double flops[LYAP_NUM_PHASES] = {};  // algorithmic flops per phase (host-side count)
+  // batched solves: worker contexts, each on its own non-blocking stream
+  std::vector<lyap_ctx*> pool;
+  std::vector<cudaStream_t> pool_streams;
 };
 
 namespace lyap {
@@ -933,8 +943,10 @@ int lyap_ctx_destroy(lyap_ctx_t* C) {
                 &C->Lm, &C->Zs, &C->Zbest, &C->G, &C->gram, &C->ysol, &C->ybest, &C->ytmp, &C->Lw, &C->Sd,
                 &C->Vs, &C->Lst, &C->Rtau, &C->Bm, &C->VB, &C->qrBar, &C->qrStatus, &C->qrCand, &C->qrNorms, &C->qrPiv, &C->qrRdiag, &C->qrWork,
                 &C->qrRank, &C->eigWork32, &C->eigX, &C->eigR, &C->eigS, &C->eigHX, &C->eigE, &C->eigLam,
-                &C->eigRed, &C->eigW, &C->eigPv, &C->eigInt};
+                &C->eigRed, &C->eigW, &C->eigPv, &C->eigInt, &C->At, &C->Ct, &C->ZY, &C->adjT};
   for (Buf* b : all) free_buf(*b);
+  for (lyap_ctx* w : C->pool) lyap_ctx_destroy(w);
+  for (cudaStream_t st : C->pool_streams) cudaStreamDestroy(st);
   if (C->hpin) cudaFreeHost(C->hpin);
   if (C->e0) cudaEventDestroy(C->e0);
   if (C->e1) cudaEventDestroy(C->e1);
@@ -1683,6 +1695,71 @@ static int adjoint_entry(lyap_ctx_t* Cp, const double* A, int64_t n, int64_t lda
   inf->status = st;
   return st;
 }
+
+// Independent Cholesky-type IR solves (config of many small equations) run concurrently:
+// worker host threads, each with its own context and non-blocking stream, take the
+// equations largest-n^3 first from a shared counter.  Every solve is the single-equation
+// lyap_solve_ir path, so each result equals what a lone call would return.
+static int batched_entry(lyap_ctx_t* C, int nb, const double* const* A, const int64_t* n, const double* const* L,
+                         const int64_t* m, const lyap_opts_t* opts, double* const* Z, const int64_t* z_cap,
+                         int64_t* rank_out, lyap_info_t* info, int workers) {
+  if (!C || nb < 0 || !opts) return LYAP_ERR_ARG;
+  if (nb == 0) return LYAP_OK;
+  if (!A || !n || !L || !m || !Z || !z_cap || !rank_out) return LYAP_ERR_ARG;
+  for (int e = 0; e < nb; ++e)
+    if (!A[e] || !L[e] || !Z[e] || n[e] <= 0 || m[e] <= 0 || z_cap[e] <= 0) return LYAP_ERR_ARG;
+  if (workers <= 0) workers = 8;
+  workers = std::max(1, std::min({workers, nb, 32}));
+  // inputs were produced on the caller's stream
+  LYAP_CUDA_TRY(cudaStreamSynchronize(C->s));
+  while ((int)C->pool.size() < workers) {
+    cudaStream_t st = nullptr;
+    LYAP_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    lyap_ctx_t* w = nullptr;
+    const int r = lyap_ctx_create(&w, st);
+    if (r < 0) {
+      cudaStreamDestroy(st);
+      return r;
+    }
+    C->pool.push_back(w);
+    C->pool_streams.push_back(st);
+  }
+  std::vector<int> order(nb);
+  for (int e = 0; e < nb; ++e) order[e] = e;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
+  std::atomic<int> next{0};
+  std::vector<int> status(nb, 0);
+  std::mutex mu;
+  std::string first_err;
+  const int dev = C->device;
+  auto work = [&](int wi) {
+    cudaSetDevice(dev);
+    lyap_ctx_t* W = C->pool[wi];
+    for (;;) {
+      const int k = next.fetch_add(1);
+      if (k >= nb) break;
+      const int e = order[k];
+      lyap_info_t* inf = info ? &info[e] : nullptr;
+      const int st = solve_entry(W, A[e], n[e], n[e], L[e], n[e], m[e], nullptr, 0, opts, Z[e], n[e], z_cap[e],
+                                 nullptr, &rank_out[e], inf, true);
+      status[e] = st;
+      if (st < 0) {
+        std::lock_guard<std::mutex> g(mu);
+        if (first_err.empty()) first_err = std::string("equation ") + std::to_string(e) + ": " + g_err;
+      }
+    }
+  };
+  std::vector<std::thread> th;
+  for (int wi = 0; wi < workers; ++wi) th.emplace_back(work, wi);
+  for (auto& t : th) t.join();
+  int ret = LYAP_OK;
+  for (int e = 0; e < nb; ++e) {
+    if (status[e] < 0 && ret >= 0) ret = status[e];
+    else if (status[e] > 0 && ret == LYAP_OK) ret = status[e];
+  }
+  if (!first_err.empty()) snprintf(g_err, sizeof(g_err), "%s", first_err.c_str());
+  return ret;
+}
 }  // namespace lyap
 
 extern "C" {
@@ -1697,6 +1774,12 @@ int lyap_solve_ir(lyap_ctx_t* C, const double* A, int64_t n, int64_t lda, const 
                   const double* S, int64_t lds, const lyap_opts_t* opts, double* Z, int64_t ldz, int64_t z_cap,
                   double* D, int64_t* rank_out, lyap_info_t* info) {
   return solve_entry(C, A, n, lda, L, ldl, m, S, lds, opts, Z, ldz, z_cap, D, rank_out, info, true);
+}
+
+int lyap_solve_ir_batched(lyap_ctx_t* C, int nb, const double* const* A, const int64_t* n, const double* const* L,
+                          const int64_t* m, const lyap_opts_t* opts, double* const* Z, const int64_t* z_cap,
+                          int64_t* rank_out, lyap_info_t* info, int workers) {
+  return batched_entry(C, nb, A, n, L, m, opts, Z, z_cap, rank_out, info, workers);
 }
 
 int lyap_adjoint(lyap_ctx_t* C, const double* A, int64_t n, int64_t lda, const double* L, int64_t ldl, int64_t m,

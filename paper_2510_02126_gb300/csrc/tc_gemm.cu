@@ -15,6 +15,8 @@
 #include "gj_inverse.cuh"
 #include "tc_gemm.cuh"
 
+#include <atomic>
+
 namespace lyap {
 
 constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 4;
@@ -243,14 +245,14 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 static EncodeTiledFn get_encode() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
+  static const EncodeTiledFn fn = []() -> EncodeTiledFn {  // initialised once, thread-safe
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = (EncodeTiledFn)p;
-  }
+      return (EncodeTiledFn)p;
+    return nullptr;
+  }();
   return fn;
 }
 
@@ -290,7 +292,7 @@ static int cached_map(MapCache* cache, int ncache, const void* ptr, int prec, in
       return LYAP_OK;
     }
   }
-  static int victim = 0;
+  static thread_local int victim = 0;
   MapCache& c = cache[victim++ % ncache];
   LYAP_TRY(make_map(&c.map, ptr, prec, rows, cols, ld));
   c.ptr = ptr;
@@ -301,10 +303,12 @@ static int cached_map(MapCache* cache, int ncache, const void* ptr, int prec, in
   *out = c.map;
   return LYAP_OK;
 }
-static MapCache g_cache[16];
+// per host thread: contexts used from different threads (batched solves) keep their own
+// tensor maps and status word
+static thread_local MapCache g_cache[16];
 
 static int* status_word() {
-  static int* p = nullptr;
+  static thread_local int* p = nullptr;
   if (!p) {
     if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
     cudaMemset(p, 0, sizeof(int));
@@ -314,11 +318,11 @@ static int* status_word() {
 
 static int launch_tc(int mode, int prec, const CUtensorMap& a, const CUtensorMap& b, int M, int N, int K,
                      const EpiGJ& eg, const EpiProd& ep, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<bool> attr{false};
+  if (!attr.load()) {
     LYAP_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
     LYAP_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-    attr = true;
+    attr.store(true);
   }
   int* st = status_word();
   if (!st) return LYAP_ERR_NOMEM;
@@ -334,7 +338,7 @@ static int launch_tc(int mode, int prec, const CUtensorMap& a, const CUtensorMap
 int tc_status_read(int* out) {
   int* st = status_word();
   if (!st) return LYAP_ERR_NOMEM;
-  LYAP_CUDA_TRY(cudaMemcpy(out, st, sizeof(int), cudaMemcpyDeviceToHost));
+  LYAP_CUDA_TRY(cudaMemcpy(out, st, sizeof(int), cudaMemcpyDeviceToHost));  // after the caller's stream sync
   return LYAP_OK;
 }
 

@@ -84,6 +84,9 @@ SIGNATURES = {
                                 C.POINTER(_D)]),
     "lyap_invert": (C.c_int, [_P, _P, _I64, _I64, C.c_int, _P, _I64, _P, C.POINTER(_D)]),
     "lyap_invert_noalloc": (C.c_int, [_P, _I64, _I64, C.c_int, _P, _I64, _P, C.POINTER(_D), _P]),
+    "lyap_solve_ir_batched": (C.c_int, [_P, C.c_int, C.POINTER(_P), C.POINTER(_I64), C.POINTER(_P), C.POINTER(_I64),
+                                        C.POINTER(LyapOpts), C.POINTER(_P), C.POINTER(_I64), C.POINTER(_I64),
+                                        C.POINTER(LyapInfo), C.c_int]),
     "lyap_adjoint": (C.c_int, [_P, _P, _I64, _I64, _P, _I64, _I64, _P, _I64, _P, _I64, _I64, _P, _P, _I64, _I64,
                                C.POINTER(LyapOpts), _P, _I64, _P, _I64, _P, _I64, _P, _I64, _I64, C.POINTER(_I64),
                                C.POINTER(LyapInfo)]),
@@ -225,6 +228,31 @@ def _solve(fn_name: str, A, L, S=None, z_cap=None, opts: LyapOpts | None = None,
 def solve_ir(A, L, S=None, z_cap=None, opts=None, **kw):
     """Mixed-precision IR (Algorithms IR-Chol / IR-LDLT): returns (Z, D, info)."""
     return _solve("lyap_solve_ir", A, L, S, z_cap, opts if opts is not None else make_opts(**kw))
+
+
+def solve_ir_batched(As, Ls, opts=None, workers=8, z_caps=None, raise_on_error=True, **kw):
+    """Independent Cholesky-type IR solves in one call (lyap_solve_ir_batched).
+    Returns (list of Z_e, list of LyapInfo, status)."""
+    ctx = context()
+    nb = len(As)
+    As = [_cm(a) for a in As]
+    Ls = [_cm(l) for l in Ls]
+    ns = [a.shape[0] for a in As]
+    caps = [int(c) for c in z_caps] if z_caps is not None else list(ns)
+    Zs = [cm_empty(n, c, a.device) for n, c, a in zip(ns, caps, As)]
+    PA = (_P * nb)(*[a.data_ptr() for a in As])
+    PL = (_P * nb)(*[l.data_ptr() for l in Ls])
+    PZ = (_P * nb)(*[z.data_ptr() for z in Zs])
+    N = (_I64 * nb)(*ns)
+    M = (_I64 * nb)(*[l.shape[1] for l in Ls])
+    CAP = (_I64 * nb)(*caps)
+    R = (_I64 * nb)()
+    infos = (LyapInfo * nb)()
+    o = opts if opts is not None else make_opts(**kw)
+    st = ctx.lib.lyap_solve_ir_batched(ctx.h, nb, PA, N, PL, M, C.byref(o), PZ, CAP, R, infos, int(workers))
+    if raise_on_error:
+        _check(st)
+    return [z[:, : R[e]] for e, z in enumerate(Zs)], list(infos), st
 
 
 def sign_solve(A, L, S=None, z_cap=None, opts=None, **kw):
@@ -375,5 +403,6 @@ lyap_residual = residual
 lyap_invert = invert
 lyap_invert_noalloc = invert_noalloc
 lyap_adjoint = adjoint
+lyap_solve_ir_batched = solve_ir_batched
 lyap_rank_trunc = rank_trunc
 lyap_sym_eig = sym_eig
