@@ -321,7 +321,15 @@ def run_case(args):
     solve:<u_s>         one lyap_solve_ir of the benchmark workload
     batched:<count>     <count> random stable equations, n log-uniform in [64, 1024], rank 1..8,
                         FP16-inner IR to 1e-12: lyap_solve_ir_batched against looped lyap_solve_ir
-                        (host wall clock; prints one JSON line)"""
+                        (host wall clock; prints one JSON line)
+    sweep3:<n>          LDL^T condition sweep (A = Q T Q^T normal 2 x 2 blocks, p = 1..4, W = L S L^T
+                        indefinite, m = 8): attainable residual and time for FP16, BF16, FP32 inner
+                        solves and the FP64 sign-Newton solve (one JSON line per run)
+    adjoint:<n>[:<k>]   forward FP16-inner IR + lyap_adjoint of l = trace(C X C^T) (p = 2 family,
+                        m = 4, C 4 x n): times, and central differences of the forward solver on
+                        k (default 20) random directions of A and L (relative errors)
+    config1             FP64 sign-Newton on the 8 x 8-grid Laplacian (n = 64, determinantal scaling,
+                        Frobenius stop 1e-12 n): microseconds per solve (CUDA events)"""
     import numpy as np
     import torch
     from paper_2510_02126_gb300 import lyap
@@ -376,6 +384,102 @@ def run_case(args):
                           "batched_solves_per_s": count / tb, "looped_solves_per_s": count / tl,
                           "speedup": tl / tb, "workers": 8,
                           "looped_converged": sum(int(i.converged) for i in infos1 if i is not None)}))
+        return 0
+    elif kind == "sweep3":
+        import time
+        import lyapgen
+        n = int(rest[0]) if rest else 1024
+        for p in (1, 2, 3, 4):
+            d = lyapgen.normal_blocks(n=n, p=p, m=8, indefinite=True)
+            A, L, S = (torch.tensor(d[k], device=dev) for k in ("A", "L", "S"))
+            lam = np.linalg.eigvals(d["A"])
+            kap = float(np.max(np.abs(lam[:, None] + lam[None, :])) / np.min(np.abs(lam[:, None] + lam[None, :])))
+            for u in ("fp16", "bf16", "fp32", "fp64"):
+                o = lyap.make_opts(u_s=u, tau_ir=TAU, imax=20)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                fn = lyap.sign_solve if u == "fp64" else lyap.solve_ir
+                try:
+                    Z, D, info = fn(A, L, S, opts=o)
+                    torch.cuda.synchronize()
+                    dt = time.perf_counter() - t0
+                    print(json.dumps({"case": "sweep3", "n": n, "p": p, "kappa_eig_ratio": kap, "u_s": u,
+                                      "solver": "sign_newton" if u == "fp64" else "ir", "status": info.status,
+                                      "converged": bool(info.converged or (u == "fp64" and info.res_final <= TAU)),
+                                      "res_final": info.res_final, "ir_steps": info.ir_steps, "rank": info.rank,
+                                      "inversions": info.n_inversions, "seconds": dt}), flush=True)
+                except lyap.LyapError as e:
+                    print(json.dumps({"case": "sweep3", "n": n, "p": p, "u_s": u, "error": str(e)}), flush=True)
+        return 0
+    elif kind == "adjoint":
+        import time
+        import lyapgen
+        n = int(rest[0]) if rest else 1024
+        d = lyapgen.normal_blocks(n=n, p=2, m=4, indefinite=False)
+        Cm = lyapgen.loss_weights(4, n)
+        A, L, C = torch.tensor(d["A"], device=dev), torch.tensor(d["L"], device=dev), torch.tensor(Cm, device=dev)
+        o = lyap.make_opts(u_s="fp16", tau_ir=1e-13, imax=30)
+        o64 = lyap.make_opts(u_s="fp64", tau_ir=1e-15, imax=10)  # the finite differences in FP64
+
+        def loss(Aa, Ll, opts):
+            Z, _, inf = lyap.solve_ir(Aa, Ll, opts=opts)
+            CZ = C @ Z
+            return float((CZ * CZ).sum()), Z, inf
+
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        l0, Z, inf = loss(A, L, o)
+        torch.cuda.synchronize()
+        t_fwd = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        out = lyap.adjoint(A, L, Z, C, opts=o)
+        torch.cuda.synchronize()
+        t_adj = time.perf_counter() - t0
+        g = np.random.default_rng(20251003)
+        h = 1e-6
+        dirs = int(rest[1]) if len(rest) > 1 else 20
+        rel_A, rel_L, nrm_A, nrm_L = [], [], [], []
+        gA, gL = float(out["dA"].norm()), float(out["dL"].norm())
+        for _ in range(dirs):
+            E = torch.tensor(g.standard_normal((n, n)), device=dev)
+            E *= A.norm() / E.norm()
+            fd = (loss(A + h * E, L, o64)[0] - loss(A - h * E, L, o64)[0]) / (2 * h)
+            an = float((out["dA"] * E).sum())
+            rel_A.append(abs(fd - an) / abs(an))
+            nrm_A.append(abs(fd - an) / (gA * float(E.norm())))
+            F = torch.tensor(g.standard_normal((n, 4)), device=dev)
+            F *= L.norm() / F.norm()
+            fd = (loss(A, L + h * F, o64)[0] - loss(A, L - h * F, o64)[0]) / (2 * h)
+            an = float((out["dL"] * F).sum())
+            rel_L.append(abs(fd - an) / abs(an))
+            nrm_L.append(abs(fd - an) / (gL * float(F.norm())))
+        mx = lambda v: max(v) if v else None  # noqa: E731
+        print(json.dumps({"case": "adjoint", "n": n, "u_s": "fp16", "forward_res": inf.res_final,
+                          "forward_rank": inf.rank, "adjoint_res": out["info"].res_final,
+                          "adjoint_inversions": out["info"].n_inversions,
+                          "forward_seconds": t_fwd, "adjoint_seconds": t_adj, "fd_directions": dirs, "fd_step": h,
+                          "fd_precision": "fp64 refinement, tau 1e-15",
+                          "max_rel_err_dA": mx(rel_A), "max_rel_err_dL": mx(rel_L),
+                          "max_err_dA_over_grad_norm": mx(nrm_A), "max_err_dL_over_grad_norm": mx(nrm_L)}))
+        return 0
+    elif kind == "config1":
+        import lyapgen
+        d = lyapgen.fp64_laplacian(grid=8, m=2)
+        A, L = torch.tensor(d["A"], device=dev), torch.tensor(d["L"], device=dev)
+        o = lyap.make_opts(u_s="fp64", scaling="det", newton_norm_fro=1, tau_newton=1e-12 * 64, rank_tol=1e-14, rho=0.0)
+        for _ in range(5):
+            lyap.sign_solve(A, L, opts=o)
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 50
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            Z, _, info = lyap.sign_solve(A, L, opts=o)
+        e1.record(stream)
+        e1.synchronize()
+        print(json.dumps({"case": "config1", "n": 64, "us_per_solve": 1000.0 * e0.elapsed_time(e1) / reps,
+                          "res_final": info.res_final, "newton_iterations": info.newton_max, "rank": info.rank}))
         return 0
     else:
         raise SystemExit(f"unknown case {args.case}")

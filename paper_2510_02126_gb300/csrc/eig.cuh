@@ -32,11 +32,12 @@ struct EigScratch {
 
 // H (q x q, ldh, FP64, symmetric; not modified) = Q diag(w) Q^T, w ascending,
 // Q (q x q, ldq).  FP32 Jacobi (two-sided in shared memory for q <= 160, block
-// one-sided on the shifted matrix H + 2 ||H||_F I across the GPU beyond), then (refine != 0) FP64
-// refinement: Ogita-Aishima steps, Newton-Schulz re-orthonormalisation, and
-// re-diagonalisation of every remaining eigenvalue cluster (its block of
-// X^T H X, shifted and scaled to unit size, by a batched FP32 Jacobi), repeated
-// until the coupling left is below 1e-15 ||H||_2.
+// two-sided across the GPU beyond), then FP64 refinement: Ogita-Aishima steps and
+// re-diagonalisation of every remaining eigenvalue cluster (its block of X^T H X,
+// shifted and scaled to unit size, by the FP32 Jacobi).
+// refine: 0 = FP32 result; 1 = FP64-accurate (up to 8 rounds, clusters to 1e-6);
+// 2 = FP64, fast (at most 3 rounds, clusters to 1e-4: for the projected update of the
+// refinement loop, whose next step corrects what is left).
 int sym_eig(const double* H, int64_t q, int64_t ldh, double* w, double* Q, int64_t ldq, int refine,
             EigScratch& sc, cudaStream_t s);
 

@@ -1336,7 +1336,7 @@ static int sol_upt(Ctx& C, int n, int qg, int cneg_start, const double* ups, boo
                         C.s));
   LYAP_TRY(prepare_eig(C, kr));
   mark(C, LYAP_PHASE_EIG);
-  LYAP_TRY(sym_eig(P<double>(C.H), kr, kr, P<double>(C.w), P<double>(C.Qh), kr, 1, C.eig, C.s));
+  LYAP_TRY(sym_eig(P<double>(C.H), kr, kr, P<double>(C.w), P<double>(C.Qh), kr, 2, C.eig, C.s));
   mark(C, LYAP_PHASE_SOLUPT);
   int* sel = P<int>(C.scal) + 64;
   select_kernel<<<1, 32, 0, C.s>>>(P<double>(C.w), kr, eta_s, 0, sel, P<double>(C.scal) + 31);
