@@ -120,3 +120,23 @@ def test_residual_verifier_matches_explicit():
     res = lib().residual(T(A), T(L), T(Z), S=T(S), D=T(y))
     ref = O.residual_eq41(A, Z, L @ S @ L.T, y)
     assert abs(res - ref) <= 1e-12 * ref
+
+
+@pytest.mark.parametrize("kind", ["random", "graded"])
+def test_sym_eig_fp64_accuracy_large(kind):
+    # block Jacobi (q > 160) + FP64 refinement at q = 1024: FP64-accurate pairs
+    q = 1024
+    g = gen.rng(900 + (kind == "graded"))
+    if kind == "random":
+        B = g.standard_normal((q, q))
+        H = (B + B.T) / 2
+    else:  # eigenvalues 1 .. 1e-16, the spectrum shape of the projected-update cores
+        Qm, _ = np.linalg.qr(g.standard_normal((q, q)))
+        H = (Qm * 10.0 ** (-16.0 * np.arange(q) / q)) @ Qm.T
+    w, Q = lib().sym_eig(T(H), True)
+    w, Q = N(w), N(Q)
+    nh = np.linalg.norm(H, 2)
+    assert np.max(np.abs(w - np.linalg.eigvalsh(H))) <= 1e-13 * nh
+    assert np.max(np.abs(Q.T @ Q - np.eye(q))) <= 1e-13
+    S = Q.T @ H @ Q
+    assert np.linalg.norm(S - np.diag(np.diag(S)), 2) <= 1e-13 * nh

@@ -165,3 +165,16 @@ def test_non_hurwitz_does_not_converge():
     with pytest.raises(Exception) as ei:
         lib().sign_solve(T(A), T(L), u_s="fp64", kmax=30)
     assert getattr(ei.value, "status", None) in (lib().ERR_NOCONV, lib().ERR_NONFINITE, lib().ERR_SINGULAR)
+
+
+def test_fp64_sign_newton_ldlt_nearly_full_rank():
+    # block-normal A (eigenvalues -a +- ib), indefinite W = L S L^T: the solution has rank
+    # close to n, so every compression is an order-n FP64 eigendecomposition (RankTruncLdlt)
+    d = gen.normal_blocks(n=512, p=2, m=8, indefinite=True, seed=gen.SEED_BASE + 60)
+    A, L, S = d["A"], d["L"], d["S"]
+    Z, D, info = lib().sign_solve(T(A), T(L), T(S), u_s="fp64")
+    assert info.status == 0
+    assert info.res_final <= 1e-13
+    X = (N(Z) * N(D)[None, :]) @ N(Z).T
+    Xo = O.bartels_stewart(A, L @ S @ L.T)
+    assert np.linalg.norm(X - Xo) <= 1e-11 * np.linalg.norm(Xo)
