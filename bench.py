@@ -115,6 +115,23 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """Largest value of x over the ranks of the process group (x itself for one rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, ms_max: float) -> float:
+    """Solves per second of all ranks together: every rank (one replica each) completes one
+    solve per step, and the step takes the slowest rank's time."""
+    return world * 1000.0 / ms_max if ms_max > 0 else 0.0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -200,12 +217,7 @@ def run_ours(args):
             tot += e0.elapsed_time(e1)
             infos.append(out)
         barrier()
-        ms = tot / steps
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms, infos
+        return max_over_ranks(tot / steps, world, dev), infos
 
     def solve_ir():
         Z, _, info = lyap.solve_ir(A, L, opts=opts_ir)
@@ -224,8 +236,8 @@ def run_ours(args):
     res_ir = max(i.res_final for i in infos_ir)
     res_64 = max(i.res_final for i in infos_64)
     ok_ir = all(i.converged for i in infos_ir) and res_ir <= TAU
-    value = (world * 1000.0 / ms_ir) if ok_ir else 0.0
-    v64 = (world * 1000.0 / ms_64) if res_64 <= TAU else 0.0
+    value = whole_job_rate(world, ms_ir) if ok_ir else 0.0
+    v64 = whole_job_rate(world, ms_64) if res_64 <= TAU else 0.0
 
     # end to end: pinned host inputs -> device -> solve -> factor back to the host
     A_h = torch.tensor(A_np).pin_memory()
@@ -297,7 +309,7 @@ def run_ours(args):
         "fp64_sign_newton": {"value": v64, "unit": UNIT, "ms_per_solve": ms_64, "res_final_max": res_64,
                              "inversions": infos_64[0].n_inversions},
         "speedup_vs_fp64_sign_newton": (value / v64) if v64 > 0 else None,
-        "e2e": {"value": (world * 1000.0 / ms_e2e) if ok_e2e else 0.0, "unit": UNIT,
+        "e2e": {"value": whole_job_rate(world, ms_e2e) if ok_e2e else 0.0, "unit": UNIT,
                 "h2d_bytes_per_step": int(A_np.nbytes + L_np.nbytes), "d2h_bytes_per_step": int(e2e_step.out_bytes)},
         "gpu_launches": launches,
         "roofline": roofline,
