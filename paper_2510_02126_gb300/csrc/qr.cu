@@ -21,54 +21,119 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
 }
 
 // ---------------------------------------------------------------------------
-// thin Householder QR (cooperative)
+// thin Householder QR (cooperative, with lookahead)
+//
+// Column l is owned by CTA l mod G.  Reflector j is published behind a per-column flag
+// instead of a grid barrier: the owner of column j+1 applies H_j to that column first
+// (the whole CTA on one column), forms reflector j+1, publishes it, and only then applies
+// H_j to its other columns; every CTA waits (bounded) for flag j before applying H_j.
+// The critical path per column is thus one column update and one reflector, not a grid
+// barrier plus the slowest CTA's update.
 // ---------------------------------------------------------------------------
+// Reflector of column j (rows j..m-1) in place, by the whole CTA: v below the diagonal
+// (unit leading entry implicit), beta on the diagonal, tau[j].
+template <typename T>
+__device__ void hqr_reflector(T* __restrict__ F, int64_t m, int64_t ld, int64_t j, T* __restrict__ tau, T* red) {
+  T* x = F + j + j * ld;
+  T sig = T(0);
+  for (int64_t i = 1 + threadIdx.x; i < m - j; i += blockDim.x) sig = fma(x[i], x[i], sig);
+  sig = block_sum(sig, red);
+  const T alpha = x[0];
+  T beta, tj, scale;
+  if (sig == T(0)) {
+    tj = T(0);
+    beta = alpha;
+    scale = T(0);
+  } else {
+    const T nrm = sqrt(alpha * alpha + sig);
+    beta = (alpha <= T(0)) ? nrm : -nrm;
+    tj = (beta - alpha) / beta;
+    scale = T(1) / (alpha - beta);
+  }
+  __syncthreads();
+  for (int64_t i = 1 + threadIdx.x; i < m - j; i += blockDim.x) x[i] *= scale;
+  if (threadIdx.x == 0) { x[0] = beta; tau[j] = tj; }
+}
+
+// y <- H_j y for one column y (rows j..m-1), by one warp (v, tj read L2-coherently)
+template <typename T>
+__device__ __forceinline__ void hqr_apply_warp(const T* __restrict__ v, T tj, T* __restrict__ y, int64_t len) {
+  const int lane = threadIdx.x & 31;
+  T w = T(0);
+  for (int64_t i = 1 + lane; i < len; i += 32) w = fma(__ldcg(&v[i]), y[i], w);
+  w = (warp_sum(w) + y[0]) * tj;
+  __syncwarp();
+  if (lane == 0) y[0] -= w;
+  for (int64_t i = 1 + lane; i < len; i += 32) y[i] = fma(-w, __ldcg(&v[i]), y[i]);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
-hqr_kernel(T* __restrict__ F, int64_t m, int64_t q, int64_t ld, T* __restrict__ tau, GridBar* bar,
+hqr_kernel(T* __restrict__ F, int64_t m, int64_t q, int64_t ld, T* __restrict__ tau, int* __restrict__ flags,
            int* status) {
   __shared__ T red[32];
+  __shared__ int ok_s;
   const int G = gridDim.x, b = blockIdx.x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int64_t kmax = (m < q) ? m : q;
+  if (kmax <= 0) return;
+  auto publish = [&](int64_t j) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicExch(&flags[j], 1);
+    }
+  };
+  if (b == 0) {
+    hqr_reflector<T>(F, m, ld, 0, tau, red);
+    publish(0);
+  }
   for (int64_t j = 0; j < kmax; ++j) {
-    if ((j % G) == b) {
-      // reflector of column j (this block owns it and has applied H_0..H_{j-1} to it)
-      T* x = F + j + j * ld;
-      T sig = T(0);
-      for (int64_t i = 1 + threadIdx.x; i < m - j; i += blockDim.x) sig = fma(x[i], x[i], sig);
-      sig = block_sum(sig, red);
-      const T alpha = x[0];
-      T beta, tj, scale;
-      if (sig == T(0)) {
-        tj = T(0);
-        beta = alpha;
-        scale = T(0);
-      } else {
-        const T nrm = sqrt(alpha * alpha + sig);
-        beta = (alpha <= T(0)) ? nrm : -nrm;
-        tj = (beta - alpha) / beta;
-        scale = T(1) / (alpha - beta);
+    // wait for reflector j (bounded)
+    if ((j % G) != b) {
+      if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned long long t0 = global_ns();
+        unsigned polls = 0;
+        while (atomicAdd(&flags[j], 0) == 0) {
+          if (((++polls) & 255u) == 0 && global_ns() - t0 > 2000000000ull) {
+            atomicCAS(status, 0, LYAP_ERR_TIMEOUT);
+            ok = 0;
+            break;
+          }
+        }
+        ok_s = ok;
       }
       __syncthreads();
-      for (int64_t i = 1 + threadIdx.x; i < m - j; i += blockDim.x) x[i] *= scale;
-      if (threadIdx.x == 0) { x[0] = beta; tau[j] = tj; }
+      if (!ok_s) return;
     }
-    if (!grid_sync(bar, status)) return;
-    // apply H_j to owned columns l > j, one warp per column
-    const T tj = tau[j];
-    const T* v = F + j + j * ld;  // v[0] = 1 implicit
+    const T tj = __ldcg(&tau[j]);
+    const T* v = F + j + j * ld;
+    const int64_t len = m - j;
+    // lookahead: the owner of column j+1 updates it with the whole CTA, then publishes
+    // reflector j+1 before touching its other columns
+    const int64_t l1 = j + 1;
+    if (l1 < q && (l1 % G) == b) {
+      T* y = F + j + l1 * ld;
+      T w = T(0);
+      for (int64_t i = 1 + threadIdx.x; i < len; i += blockDim.x) w = fma(__ldcg(&v[i]), y[i], w);
+      w = block_sum(w, red);
+      w = (w + y[0]) * tj;
+      __syncthreads();  // every thread has read y[0]
+      if (threadIdx.x == 0) y[0] -= w;
+      for (int64_t i = 1 + threadIdx.x; i < len; i += blockDim.x) y[i] = fma(-w, __ldcg(&v[i]), y[i]);
+      __syncthreads();
+      if (l1 < kmax) {
+        hqr_reflector<T>(F, m, ld, l1, tau, red);
+        publish(l1);
+      }
+    }
+    // the remaining owned columns l > j + 1, one warp per column
     int slot = 0;
     for (int64_t l = b; l < q; l += G) {
-      if (l <= j) continue;
+      if (l <= l1) continue;
       if ((slot++ % nw) != warp) continue;
-      T* y = F + j + l * ld;
-      T w = T(0);
-      for (int64_t i = 1 + lane; i < m - j; i += 32) w = fma(v[i], y[i], w);
-      w = warp_sum(w) + y[0];
-      w *= tj;
-      if (lane == 0) y[0] -= w;
-      for (int64_t i = 1 + lane; i < m - j; i += 32) y[i] = fma(-w, v[i], y[i]);
+      hqr_apply_warp<T>(v, tj, F + j + l * ld, len);
     }
     __syncthreads();
   }
@@ -79,8 +144,9 @@ int householder_qr(T* F, int64_t m, int64_t q, int64_t ld, T* tau, QRScratch& sc
   if (m <= 0 || q <= 0) return LYAP_OK;
   int G = (int)std::min<int64_t>(q, sc.num_sms);
   if (G < 1) G = 1;
-  LYAP_CUDA_TRY(cudaMemsetAsync(sc.bar, 0, sizeof(GridBar), s));
-  void* args[] = {&F, &m, &q, &ld, &tau, &sc.bar, &sc.status};
+  const int64_t kmax = std::min(m, q);
+  LYAP_CUDA_TRY(cudaMemsetAsync(sc.flags, 0, sizeof(int) * (size_t)kmax, s));
+  void* args[] = {&F, &m, &q, &ld, &tau, &sc.flags, &sc.status};
   LYAP_CUDA_TRY(cudaLaunchCooperativeKernel((void*)hqr_kernel<T>, dim3(G), dim3(256), args, 0, s));
   lyap_count_launch();
   return LYAP_OK;

@@ -15,6 +15,7 @@ struct QRScratch {
   void* rdiag = nullptr;    // R diagonal (>= ncols)
   void* work = nullptr;     // transposed copy of the factor (c x n values of T)
   int* rank = nullptr;      // device int: truncation rank
+  int* flags = nullptr;     // per-column ready flags of householder_qr (>= min(m, q) ints)
   int num_sms = 0;
 };
 

@@ -458,6 +458,7 @@ static int prepare_newton(Ctx& C, int n, int m, int prec) {
   C.qr.cand = C.qrCand.p;
   C.qr.norms = C.qrNorms.p;
   C.qr.piv = P<int>(C.qrPiv);
+  C.qr.flags = P<int>(C.qrPiv);  // shares the pivot buffer: QRCP and QR never run at the same time
   C.qr.rdiag = C.qrRdiag.p;
   C.qr.work = C.qrWork.p;
   C.qr.rank = P<int>(C.qrRank);
