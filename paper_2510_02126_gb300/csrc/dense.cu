@@ -9,10 +9,14 @@ namespace lyap {
 // ---------------------------------------------------------------------------
 // TILE x TILE output tile (TILE = 64 or 32), 16-deep K slices, 256 threads, each owning
 // (TILE/16) x (TILE/16) outputs.
-template <typename T, bool TA, bool TB, int TILE>
+// SYM: the result is symmetric (M == N, e.g. X^T X or X^T (H X) with H symmetric): only
+// tiles on or above the diagonal are computed; each writes its upper-triangle entries
+// (i <= j) and mirrors the strictly upper ones to (j, i), so every entry is written once.
+template <typename T, bool TA, bool TB, int TILE, bool SYM = false>
 __global__ void __launch_bounds__(256)
 gemm_kernel(int64_t M, int64_t N, int64_t K, T alpha, const T* __restrict__ A, int64_t lda,
             const T* __restrict__ B, int64_t ldb, T beta, T* __restrict__ C, int64_t ldc) {
+  if (SYM && blockIdx.x > blockIdx.y) return;
   constexpr int RA = TILE / 16;            // outputs per thread along each dimension
   constexpr int LD = TILE * 16 / 256;      // loads per thread per operand slice
   __shared__ T As[16][TILE + 1];
@@ -70,8 +74,11 @@ gemm_kernel(int64_t M, int64_t N, int64_t K, T alpha, const T* __restrict__ A, i
     for (int a = 0; a < RA; ++a) {
       const int64_t i = m0 + tx + 16 * a;
       if (i >= M) continue;
+      if (SYM && i > j) continue;  // written by the mirror of (j, i)
       T* c = C + i + j * ldc;
-      *c = (beta == T(0)) ? alpha * acc[a][b] : alpha * acc[a][b] + beta * *c;
+      const T v = (beta == T(0)) ? alpha * acc[a][b] : alpha * acc[a][b] + beta * *c;
+      *c = v;
+      if (SYM && i < j) C[j + i * ldc] = v;  // C was symmetric on entry when beta != 0
     }
   }
 }
@@ -117,6 +124,25 @@ int gemm(char ta, char tb, int64_t M, int64_t N, int64_t K, T alpha, const T* A,
 }
 template int gemm<float>(char, char, int64_t, int64_t, int64_t, float, const float*, int64_t, const float*,
                          int64_t, float, float*, int64_t, cudaStream_t);
+
+template <typename T>
+int gemm_sym(char ta, char tb, int64_t N, int64_t K, T alpha, const T* A, int64_t lda, const T* B, int64_t ldb,
+             T beta, T* C, int64_t ldc, cudaStream_t s) {
+  if (N <= 0) return LYAP_OK;
+  if (K <= 0) return gemm<T>(ta, tb, N, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
+  const bool TA = (ta == 'T' || ta == 't'), TB = (tb == 'T' || tb == 't');
+  constexpr int TILE = 32;
+  dim3 grid((unsigned)ceil_div(N, TILE), (unsigned)ceil_div(N, TILE));
+  if (TA && !TB) gemm_kernel<T, true, false, TILE, true><<<grid, 256, 0, s>>>(N, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else if (!TA && TB) gemm_kernel<T, false, true, TILE, true><<<grid, 256, 0, s>>>(N, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else if (!TA && !TB) gemm_kernel<T, false, false, TILE, true><<<grid, 256, 0, s>>>(N, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else gemm_kernel<T, true, true, TILE, true><<<grid, 256, 0, s>>>(N, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  LYAP_CUDA_TRY(cudaGetLastError());
+  lyap_count_launch();
+  return LYAP_OK;
+}
+template int gemm_sym<double>(char, char, int64_t, int64_t, double, const double*, int64_t, const double*, int64_t,
+                              double, double*, int64_t, cudaStream_t);
 template int gemm<double>(char, char, int64_t, int64_t, int64_t, double, const double*, int64_t,
                           const double*, int64_t, double, double*, int64_t, cudaStream_t);
 

@@ -8,6 +8,12 @@ namespace lyap {
 template <typename T>
 int gemm(char ta, char tb, int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t lda,
          const T* B, int64_t ldb, T beta, T* C, int64_t ldc, cudaStream_t s);
+// C (N x N) = alpha op(A) op(B) + beta C for a product known to be symmetric (e.g. X^T X,
+// X^T (H X) with H symmetric): only the upper triangle is computed and mirrored; when
+// beta != 0 C must be symmetric on entry.
+template <typename T>
+int gemm_sym(char ta, char tb, int64_t N, int64_t K, T alpha, const T* A, int64_t lda, const T* B, int64_t ldb,
+             T beta, T* C, int64_t ldc, cudaStream_t s);
 
 // Deterministic reductions into a device double (fixed block count, fixed order).
 // out[0] = sum_i x_i^2 over an m x n column-major matrix (ld).
