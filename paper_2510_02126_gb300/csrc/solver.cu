@@ -90,6 +90,7 @@ struct lyap_ctx {
   lyap::EigScratch eig;
   // adjoint: A^T, C^T, the adjoint factor and the gradient products
   lyap::Buf At, Ct, ZY, adjT;
+  lyap::Buf Hf;  // FP32 copy of the residual core for its range finder
   lyap::Buf eigWork32, eigX, eigR, eigS, eigHX, eigE, eigLam, eigRed, eigW, eigPv, eigInt;
   void* hpin = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -944,7 +945,7 @@ int lyap_ctx_destroy(lyap_ctx_t* C) {
                 &C->Lm, &C->Zs, &C->Zbest, &C->G, &C->gram, &C->ysol, &C->ybest, &C->ytmp, &C->Lw, &C->Sd,
                 &C->Vs, &C->Lst, &C->Rtau, &C->Bm, &C->VB, &C->qrBar, &C->qrStatus, &C->qrCand, &C->qrNorms, &C->qrPiv, &C->qrRdiag, &C->qrWork,
                 &C->qrRank, &C->eigWork32, &C->eigX, &C->eigR, &C->eigS, &C->eigHX, &C->eigE, &C->eigLam,
-                &C->eigRed, &C->eigW, &C->eigPv, &C->eigInt, &C->At, &C->Ct, &C->ZY, &C->adjT};
+                &C->eigRed, &C->eigW, &C->eigPv, &C->eigInt, &C->At, &C->Ct, &C->ZY, &C->adjT, &C->Hf};
   for (Buf* b : all) free_buf(*b);
   for (lyap_ctx* w : C->pool) lyap_ctx_destroy(w);
   for (cudaStream_t st : C->pool_streams) cudaStreamDestroy(st);
@@ -1235,12 +1236,17 @@ static int res_fac(Ctx& C, const Problem& pb, const double* Lw, const double* sd
   LYAP_TRY(ensure(C.Csel, (size_t)kr * kr * 8 + 64));
   int neig = kr;
   if (kr > 160) {
+    // the range is found in FP32 (the split needs FP32 accuracy at most, and the FP32 copy
+    // fits the cluster-resident QRCP); the Rayleigh-Ritz step below uses the FP64 H
     double* Zr = P<double>(C.Csel);
-    LYAP_TRY((copy_cast<double, double>(P<double>(C.H), kr, kr, kr, Zr, kr, 1.0, C.s)));
-    LYAP_TRY(qrcp_truncate<double>(Zr, kr, kr, kr, 0.1 * eta_r, C.qr, C.s));
+    LYAP_TRY(ensure(C.Hf, (size_t)kr * kr * 4 + 64));
+    float* Hf = P<float>(C.Hf);
+    LYAP_TRY((copy_cast<double, float>(P<double>(C.H), kr, kr, kr, Hf, kr, 1.0, C.s)));
+    LYAP_TRY(qrcp_truncate<float>(Hf, kr, kr, kr, 0.1 * eta_r, C.qr, C.s));
     int r = 0;
     LYAP_TRY(sync_read(C, C.qr.rank, &r, sizeof(int)));
     r = std::max(r, 1);
+    LYAP_TRY((copy_cast<float, double>(Hf, kr, r, kr, Zr, kr, 1.0, C.s)));
     LYAP_TRY(ensure(C.Rtau, (size_t)(r + 8) * 8));
     LYAP_TRY(ensure(C.Bm, (size_t)r * r * 8 + 64));
     LYAP_TRY(ensure(C.VB, (size_t)r * r * 8 + 64));
