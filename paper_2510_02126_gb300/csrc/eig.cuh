@@ -36,7 +36,7 @@ struct EigScratch {
 // re-diagonalisation of every remaining eigenvalue cluster (its block of X^T H X,
 // shifted and scaled to unit size, by the FP32 Jacobi).
 // refine: 0 = FP32 result; 1 = FP64-accurate (up to 8 rounds, clusters to 1e-6);
-// 2 = FP64, fast (at most 3 rounds, clusters to 1e-4: for the projected update of the
+// 2 = FP64, fast (at most 3 rounds, clusters to 1e-3: for the projected update of the
 // refinement loop, whose next step corrects what is left).
 int sym_eig(const double* H, int64_t q, int64_t ldh, double* w, double* Q, int64_t ldq, int refine,
             EigScratch& sc, cudaStream_t s);
