@@ -5,6 +5,8 @@
 
 namespace lyap {
 
+constexpr int EIG_MAX_Q = 1280;  // largest order sym_eig accepts (block Jacobi round-robin tables)
+
 struct EigScratch {
   float* work32 = nullptr;   // bjac_work_floats(q) floats (block Jacobi workspace)
   double* X = nullptr;       // q^2 each

@@ -1228,14 +1228,16 @@ static int res_fac(Ctx& C, const Problem& pb, const double* Lw, const double* sd
   out->rp = out->rm = 0;
   if (!want_split) return LYAP_OK;
   // eigen-split of H (FP32 accuracy suffices: the split is truncated at eta_r >> u_fp32).
-  // Large cores: the range of H is first found by QR with column pivoting truncated at
-  // eta_r / 10 (everything dropped lies far below the truncation level of the split), and
-  // the eigenpairs come from the Rayleigh-Ritz matrix on that range.
+  // Cores above the eigensolver's order limit: the range of H is first found by QR with
+  // column pivoting truncated at eta_r / 10 (everything dropped lies far below the
+  // truncation level of the split), and the eigenpairs come from the Rayleigh-Ritz matrix
+  // on that range.  Below it the direct FP32 eigensolver is cheaper: the range found is
+  // typically most of H (805 of 950 at n = 1024) and costs two QRs and three products.
   LYAP_TRY(ensure(C.w, (size_t)kr * 8 + 64));
   LYAP_TRY(ensure(C.Qh, (size_t)kr * kr * 8 + 64));
   LYAP_TRY(ensure(C.Csel, (size_t)kr * kr * 8 + 64));
   int neig = kr;
-  if (kr > 160) {
+  if (kr > EIG_MAX_Q) {
     // the range is found in FP32 (the split needs FP32 accuracy at most, and the FP32 copy
     // fits the cluster-resident QRCP); the Rayleigh-Ritz step below uses the FP64 H
     double* Zr = P<double>(C.Csel);
