@@ -472,20 +472,47 @@ qrcp_cluster_kernel(T* __restrict__ Z, int n, int c, int64_t ldz, int nc, double
       const int i = min(t >> 1, ncl - 1), h = t & 1;
       const bool live = (t < 2 * ncl) && stepof[i] < 0;
       T* y = Ms + j + (size_t)i * ldm;
-      T w = T(0);
-      if (live)
-        for (int l = 1 + h; l < c - j; l += 2) w = fma(v[l], y[l], w);
+      const int len = c - j;
+      // four independent partial sums per thread (rows l, l + 2, l + 4, l + 6): the
+      // dependent chains are a quarter as long
+      T w0 = T(0), w1 = T(0), w2 = T(0), w3 = T(0);
+      int l = 1 + h;
+      if (live) {
+        for (; l + 6 < len; l += 8) {
+          w0 = fma(v[l], y[l], w0);
+          w1 = fma(v[l + 2], y[l + 2], w1);
+          w2 = fma(v[l + 4], y[l + 4], w2);
+          w3 = fma(v[l + 6], y[l + 6], w3);
+        }
+        for (; l < len; l += 2) w0 = fma(v[l], y[l], w0);
+      }
+      T w = (w0 + w1) + (w2 + w3);
       w += __shfl_xor_sync(0xffffffffu, w, 1);
       const T y0 = live ? y[0] : T(0);
       w = (w + y0) * tj;
       const T top = y0 - w;
-      T tail2 = T(0);
-      if (live)
-        for (int l = 1 + h; l < c - j; l += 2) {
+      T t0s = T(0), t1s = T(0), t2s = T(0), t3s = T(0);
+      l = 1 + h;
+      if (live) {
+        for (; l + 6 < len; l += 8) {
+          const T n0 = fma(-w, v[l], y[l]), n1 = fma(-w, v[l + 2], y[l + 2]);
+          const T n2 = fma(-w, v[l + 4], y[l + 4]), n3 = fma(-w, v[l + 6], y[l + 6]);
+          y[l] = n0;
+          y[l + 2] = n1;
+          y[l + 4] = n2;
+          y[l + 6] = n3;
+          t0s = fma(n0, n0, t0s);
+          t1s = fma(n1, n1, t1s);
+          t2s = fma(n2, n2, t2s);
+          t3s = fma(n3, n3, t3s);
+        }
+        for (; l < len; l += 2) {
           const T nv = fma(-w, v[l], y[l]);
           y[l] = nv;
-          tail2 = fma(nv, nv, tail2);
+          t0s = fma(nv, nv, t0s);
         }
+      }
+      T tail2 = (t0s + t1s) + (t2s + t3s);
       tail2 += __shfl_xor_sync(0xffffffffu, tail2, 1);
       if (live && h == 0) {
         y[0] = top;
