@@ -40,6 +40,10 @@ struct Buf {
 static int ensure(Buf& b, size_t bytes) {
   if (bytes <= b.cap && b.p) return LYAP_OK;
   if (b.p) {
+    // work queued on this context's (non-blocking) stream may still use the old buffer;
+    // cudaFree does not wait for it, and another context's next cudaMalloc may reuse the
+    // memory at once (batched solves grow buffers on several streams concurrently)
+    LYAP_CUDA_TRY(cudaDeviceSynchronize());
     cudaFree(b.p);
     b.p = nullptr;
     b.cap = 0;
@@ -50,6 +54,11 @@ static int ensure(Buf& b, size_t bytes) {
     lyap_set_error_message("device allocation failed", __FILE__, __LINE__);
     return LYAP_ERR_NOMEM;
   }
+  // zero-filled, and complete before any kernel of any stream touches it: status words and
+  // flags are read as "no error" before their first write (memory freed by an earlier
+  // context comes back holding its old contents)
+  LYAP_CUDA_TRY(cudaMemset(b.p, 0, want));
+  LYAP_CUDA_TRY(cudaDeviceSynchronize());
   b.cap = want;
   return LYAP_OK;
 }
@@ -733,6 +742,9 @@ static int newton_run(Ctx& C, int n, int c0, bool ldlt, const NewtonOpts& o, boo
   int K = compute ? o.kmax : C.store_count;
   if (compute) {
     C.store_count = 0;
+    // the compressions below report through the QR status word: clear what an earlier call
+    // left in it
+    LYAP_CUDA_TRY(cudaMemsetAsync(C.qr.status, 0, sizeof(int), C.s));
     newton_init_kernel<<<1, 1, 0, C.s>>>(st, o.scaling);
     lyap_count_launch();
     LYAP_TRY(sumsq<T>(P<T>(C.A0), n, n, n, &st->ssA, P<double>(C.part), C.s));

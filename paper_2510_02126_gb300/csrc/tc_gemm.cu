@@ -311,7 +311,8 @@ static int* status_word() {
   static thread_local int* p = nullptr;
   if (!p) {
     if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
-    cudaMemset(p, 0, sizeof(int));
+    // cleared before any kernel (on any stream) can report into it
+    if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return nullptr;
   }
   return p;
 }
