@@ -47,3 +47,31 @@ def test_batched_reports_a_failing_equation():
     assert infos[2].status < 0
     for k in (0, 1, 3, 4):
         assert infos[k].status >= 0 and infos[k].converged, k
+
+
+def test_batched_on_fresh_contexts_after_destroyed_ones():
+    # Worker contexts created after earlier contexts were destroyed receive recycled device
+    # memory: every status word must be cleared before its first read (regression: a stale
+    # nonzero word aborted solves with a random status or cut the first Newton solve short).
+    import gc
+
+    lp = lib()
+    # the batched workload family (32 equations, n 64..1017, rank 1..8), all of which
+    # converge in at most 7 FP16-inner refinement steps
+    eqs = gen.batch_uneven(count=32, nmin=64, nmax=1024, rmax=8)
+    As, Ls = [T(e["A"]) for e in eqs], [T(e["L"]) for e in eqs]
+    o = lp.make_opts(u_s="fp16", tau_ir=1e-12, imax=10)
+    try:
+        for rep in range(3):
+            if lp._ctx is not None:
+                lp._ctx.close()
+                lp._ctx = None
+            gc.collect()
+            Zs, infos, st = lp.solve_ir_batched(As, Ls, opts=o, workers=8, raise_on_error=False)
+            assert st == 0, (rep, st)
+            for k, inf in enumerate(infos):
+                assert inf.converged and inf.res_final <= 1e-12, (rep, k, inf.status, inf.res_final)
+    finally:
+        if lp._ctx is not None:
+            lp._ctx.close()
+            lp._ctx = None
