@@ -331,6 +331,8 @@ def run_case(args):
                         H = T P T^T (T upper triangular, P = diag(+-1)), the shape of the
                         residual cores of the refinement
     solve:<u_s>         one lyap_solve_ir of the benchmark workload
+    table41[:n,n]       the Sec. 4.2 synthetic study (Table 4.1): both forms, bf16 / fp16 / fp32
+                        inner precisions and the FP64 solver over the eight q, n = 100 and 1000
     batched:<count>     <count> random stable equations, n log-uniform in [64, 1024], rank 1..8,
                         FP16-inner IR to 1e-12: lyap_solve_ir_batched against looped lyap_solve_ir
                         (host wall clock; prints one JSON line)
@@ -396,6 +398,49 @@ def run_case(args):
                           "batched_solves_per_s": count / tb, "looped_solves_per_s": count / tl,
                           "speedup": tl / tb, "workers": 8,
                           "looped_converged": sum(int(i.converged) for i in infos1 if i is not None)}))
+        return 0
+    elif kind == "table41":
+        # Sec. 4.2 synthetic study (the generator of Table 4.1): n in {100, 1000}, the eight
+        # q of the table (kappa_2 of the Lyapunov operator = 10^q), Cholesky and LDL^T forms
+        # (S = I_m, as the paper sets it), inner precisions bf16 / fp16 / fp32 and the plain
+        # FP64 sign-Newton solver; library defaults otherwise (tau_ir = n u, imax = 50).
+        # Prints res, varsigma(alpha) (= newton_total(newton_max)) and rank per run, with the
+        # counts Table 4.1 prints where the golden file holds them.
+        import time
+        import lyapgen
+        gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden",
+                                           "table41_fp64_newton_counts.json")))
+        g32 = gold["fp32_inner_iter_u64_n100_chol"]
+        ns = [int(x) for x in rest[0].split(",")] if rest else [100, 1000]
+        for n in ns:
+            for qi, q in enumerate(gold["q"]):
+                d = lyapgen.paper_synthetic(n, q)
+                A, L = torch.tensor(d["A"], device=dev), torch.tensor(d["L"], device=dev)
+                m = d["L"].shape[1]
+                for form in ("chol", "ldlt"):
+                    S = torch.eye(m, dtype=torch.float64, device=dev) if form == "ldlt" else None
+                    for u in ("bf16", "fp16", "fp32", "fp64"):
+                        o = lyap.make_opts(u_s=u)
+                        rec = {"case": "table41", "n": n, "q": q, "cond_printed": gold["cond_printed"][qi],
+                               "form": form, "u_s": u, "solver": "sign_newton" if u == "fp64" else "ir"}
+                        if u == "fp64":
+                            rec["alpha_printed"] = gold["alpha"][str(n)][form][qi]
+                        if u == "fp32" and n == 100 and form == "chol" and q in g32["q"]:
+                            k = g32["q"].index(q)
+                            rec["varsigma_alpha_printed"] = [g32["total"][k], g32["alpha"][k]]
+                        torch.cuda.synchronize()
+                        t0 = time.perf_counter()
+                        try:
+                            fn = lyap.sign_solve if u == "fp64" else lyap.solve_ir
+                            Z, D, info = fn(A, L, S, opts=o)
+                            torch.cuda.synchronize()
+                            rec.update({"status": info.status, "converged": bool(info.converged),
+                                        "res_final": info.res_final, "varsigma": info.newton_total,
+                                        "alpha": info.newton_max, "ir_steps": info.ir_steps, "rank": info.rank,
+                                        "seconds": time.perf_counter() - t0})
+                        except lyap.LyapError as e:
+                            rec["error"] = str(e)
+                        print(json.dumps(rec), flush=True)
         return 0
     elif kind == "sweep3":
         import time
