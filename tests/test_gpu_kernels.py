@@ -140,3 +140,22 @@ def test_sym_eig_fp64_accuracy_large(kind):
     assert np.max(np.abs(Q.T @ Q - np.eye(q))) <= 1e-13
     S = Q.T @ H @ Q
     assert np.linalg.norm(S - np.diag(np.diag(S)), 2) <= 1e-13 * nh
+
+
+@pytest.mark.parametrize("refine", [False, True])
+def test_sym_eig_order_beyond_split_grid(refine):
+    # q = 1260: 79 block pairs, so 2 x 79 CTAs exceed the 152 SMs of a GB300 and the block
+    # Jacobi runs without a separate eigenvector side (each pair CTA also updates V);
+    # below the order limit 1280, with a padded tail (1260 = 78 x 16 + 12)
+    q = 1260
+    g = gen.rng(1260)
+    B = g.standard_normal((q, q))
+    H = (B + B.T) / 2
+    w, Q = lib().sym_eig(T(H), refine)
+    w, Q = N(w), N(Q)
+    nh = np.linalg.norm(H, 2)
+    tol = 1e-13 if refine else 2e-5
+    assert np.max(np.abs(w - np.linalg.eigvalsh(H))) <= tol * nh * (1 if refine else q ** 0.5)
+    assert np.max(np.abs(Q.T @ Q - np.eye(q))) <= (1e-13 if refine else 1e-4)
+    S = Q.T @ H @ Q
+    assert np.linalg.norm(S - np.diag(np.diag(S)), 2) <= tol * nh * (1 if refine else q ** 0.5)
