@@ -1769,6 +1769,8 @@ static int batched_entry(lyap_ctx_t* C, int nb, const double* const* A, const in
         if (first_err.empty()) first_err = std::string("equation ") + std::to_string(e) + ": " + g_err;
       }
     }
+    // every solve of this thread has completed (solve_entry waits for its last event)
+    tc_release_thread_state();
   };
   std::vector<std::thread> th;
   for (int wi = 0; wi < workers; ++wi) th.emplace_back(work, wi);

@@ -307,8 +307,9 @@ static int cached_map(MapCache* cache, int ncache, const void* ptr, int prec, in
 // tensor maps and status word
 static thread_local MapCache g_cache[16];
 
+static thread_local int* g_status = nullptr;
 static int* status_word() {
-  static thread_local int* p = nullptr;
+  int*& p = g_status;
   if (!p) {
     if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
     // cleared before any kernel (on any stream) can report into it
@@ -334,6 +335,15 @@ static int launch_tc(int mode, int prec, const CUtensorMap& a, const CUtensorMap
   LYAP_CUDA_TRY(cudaGetLastError());
   lyap_count_launch();
   return LYAP_OK;
+}
+
+// Frees the calling thread's status word (a worker thread about to exit, its work finished);
+// the next use on this thread allocates a fresh one.
+void tc_release_thread_state() {
+  if (g_status) {
+    cudaFree(g_status);
+    g_status = nullptr;
+  }
 }
 
 int tc_status_read(int* out) {

@@ -29,6 +29,8 @@ int tc_product(int prec, int n, int c, const void* Xs, const int* eX, const void
 // tc_product with one power-of-two exponent per column.
 // Reads (and clears) the status word of the tensor-core kernels (0 or LYAP_ERR_TIMEOUT).
 int tc_status_read(int* out);
+// Release the calling host thread's status word (call before the thread exits).
+void tc_release_thread_state();
 
 int factor_to_16(int prec, const float* Z, int n, int c, int64_t ld, void* Zh, int* eZ, cudaStream_t s);
 
