@@ -222,6 +222,18 @@ int lyap_residual(lyap_ctx_t* ctx, const double* A, int64_t n, int64_t lda,
                   const double* Z, int64_t ldz, int64_t r, const double* D, double* res_out);
 
 /*
+ * The loss of the differentiable solve and its gradient in C (no counterpart in the
+ * paper: the loss l = trace(C X C^T) is the one the adjoint entry point differentiates):
+ *   *loss = trace(C X C^T) = sum_j D_j ||C z_j||^2,   dC = dl/dC = 2 C X  (q x n, lddc),
+ * X = Z diag(D) Z^T (D == NULL: X = Z Z^T), in FP64 from the factor (C Z, no n x n matrix).
+ *   Z (n x r, ldz), D (r or NULL), Cm (q x n, ldc): DEVICE, column-major FP64
+ *   loss  HOST double;  dC optional DEVICE output (NULL to skip)
+ * Returns LYAP_OK or LYAP_ERR_ARG / LYAP_ERR_CUDA / LYAP_ERR_NOMEM.
+ */
+int lyap_trace_loss(lyap_ctx_t* ctx, const double* Z, int64_t n, int64_t ldz, int64_t r, const double* D,
+                    const double* Cm, int64_t ldc, int64_t q, double* loss, double* dC, int64_t lddc);
+
+/*
  * Dense inversion behind every Newton step (Sec. 3.3 cost model: 2 n^3 flops):
  * blocked Gauss-Jordan elimination with partial pivoting -- the getrf pivot
  * sequence (largest |a_ij| in the active column, lowest row on ties) fused with

@@ -361,10 +361,10 @@ static int launch_panel(GJWork& W, int k, int step, cudaStream_t s) {
     return LYAP_ERR_ARG;
   }
   auto kern = gj_panel_kernel<T, NW, RPT, CL, OP>;
-  static std::atomic<bool> attr_set{false};
-  if (CL && !attr_set.load()) {
+  static DeviceOnce attr_set;
+  if (CL && attr_set.need()) {
     LYAP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    attr_set.store(true);
+    attr_set.set();
   }
   const T* Mcur = (const T*)W.M[W.cur];
   T* Mnew = (T*)W.M[1 - W.cur];

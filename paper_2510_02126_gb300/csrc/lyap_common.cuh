@@ -6,6 +6,7 @@
 #include <stdint.h>
 #include <math.h>
 #include <algorithm>
+#include <atomic>
 
 #include "../../include/liblyap.h"
 
@@ -29,6 +30,28 @@ void lyap_set_error_message(const char* what, const char* file, int line);
 void lyap_count_launch(int k = 1);
 
 static inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// One-time host actions per device: kernel attributes set with cudaFuncSetAttribute apply
+// to the device that is current at the call, so a flag shared by the whole process would
+// skip them on every device but the first.  need() is true until set() has run with the
+// same device current.
+constexpr int LYAP_MAX_DEVICES = 64;
+struct DeviceOnce {
+  std::atomic<bool> done[LYAP_MAX_DEVICES] = {};
+  static int device() {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess) { cudaGetLastError(); return -1; }
+    return d;
+  }
+  bool need() const {
+    const int d = device();
+    return d < 0 || d >= LYAP_MAX_DEVICES || !done[d].load();
+  }
+  void set() {
+    const int d = device();
+    if (d >= 0 && d < LYAP_MAX_DEVICES) done[d].store(true);
+  }
+};
 
 // Device spin-waits never run unbounded: after this many polls a kernel records
 // LYAP_ERR_TIMEOUT in its status word and returns.

@@ -566,11 +566,11 @@ int qrcp_truncate(T* Z, int64_t n, int64_t c, int64_t ldz, double tol, QRScratch
     auto kc = qrcp_cluster_kernel<T>;
     // attributes are set once, to their largest value: concurrent callers (batched
     // solves) must never lower them between another caller's set and launch
-    static std::atomic<bool> attr_c{false};
-    if (!attr_c.load()) {
+    static DeviceOnce attr_c;
+    if (attr_c.need()) {
       LYAP_CUDA_TRY(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)QRCP_CLUSTER_SMEM));
       LYAP_CUDA_TRY(cudaFuncSetAttribute(kc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-      attr_c.store(true);
+      attr_c.set();
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(CL);
@@ -597,10 +597,10 @@ int qrcp_truncate(T* Z, int64_t n, int64_t c, int64_t ldz, double tol, QRScratch
     lyap_set_error_message("QR with column pivoting: factor too wide", __FILE__, __LINE__);
     return LYAP_ERR_ARG;
   }
-  static std::atomic<bool> attr_g{false};
-  if (smem > 48 * 1024 && !attr_g.load()) {
+  static DeviceOnce attr_g;
+  if (smem > 48 * 1024 && attr_g.need()) {
     LYAP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)QRCP_CLUSTER_SMEM));
-    attr_g.store(true);
+    attr_g.set();
   }
   LYAP_CUDA_TRY(cudaMemsetAsync(sc.bar, 0, sizeof(GridBar), s));
   T* M = (T*)sc.work;

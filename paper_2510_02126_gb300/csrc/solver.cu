@@ -99,6 +99,7 @@ struct lyap_ctx {
   lyap::EigScratch eig;
   // adjoint: A^T, C^T, the adjoint factor and the gradient products
   lyap::Buf At, Ct, ZY, adjT;
+  lyap::Buf tl;  // trace loss: C Z and C Z diag(D)
   lyap::Buf Hf;  // FP32 copy of the residual core for its range finder
   lyap::Buf eigWork32, eigX, eigR, eigS, eigHX, eigE, eigLam, eigRed, eigW, eigPv, eigInt;
   void* hpin = nullptr;
@@ -396,6 +397,27 @@ __global__ void gram_norm_kernel(const double* __restrict__ G, int c, const doub
 }
 __global__ void scale_vec_kernel(double* v, int n, double f) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] *= f;
+}
+// trace(C X C^T) = sum_j d_j sum_k T[k, j]^2 with T = C Z (q x r, column-major); d == NULL
+// means d = 1.  Also TD = T diag(d).  One block, fixed order (the same bits every call).
+__global__ void trace_loss_kernel(const double* __restrict__ Tm, int q, int r, const double* __restrict__ d,
+                                  double* __restrict__ TD, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double t = 0.0;
+  for (int64_t e = threadIdx.x; e < (int64_t)q * r; e += blockDim.x) {
+    const int64_t j = e / q;
+    const double v = Tm[e], dj = d ? d[j] : 1.0;
+    t = fma(dj * v, v, t);
+    TD[e] = dj * v;
+  }
+  t = warp_sum(t);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double u = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) u += sh[w];
+    *out = u;
+  }
 }
 // Ainv (column-major, ld) [i, perm[c]] = X[i, c] (X row-major)
 template <typename T>
@@ -957,7 +979,7 @@ int lyap_ctx_destroy(lyap_ctx_t* C) {
                 &C->Lm, &C->Zs, &C->Zbest, &C->G, &C->gram, &C->ysol, &C->ybest, &C->ytmp, &C->Lw, &C->Sd,
                 &C->Vs, &C->Lst, &C->Rtau, &C->Bm, &C->VB, &C->qrBar, &C->qrStatus, &C->qrCand, &C->qrNorms, &C->qrPiv, &C->qrRdiag, &C->qrWork,
                 &C->qrRank, &C->eigWork32, &C->eigX, &C->eigR, &C->eigS, &C->eigHX, &C->eigE, &C->eigLam,
-                &C->eigRed, &C->eigW, &C->eigPv, &C->eigInt, &C->At, &C->Ct, &C->ZY, &C->adjT, &C->Hf};
+                &C->eigRed, &C->eigW, &C->eigPv, &C->eigInt, &C->At, &C->Ct, &C->ZY, &C->adjT, &C->Hf, &C->tl};
   for (Buf* b : all) free_buf(*b);
   for (lyap_ctx* w : C->pool) lyap_ctx_destroy(w);
   for (cudaStream_t st : C->pool_streams) cudaStreamDestroy(st);
@@ -1847,6 +1869,30 @@ int lyap_residual(lyap_ctx_t* C, const double* A, int64_t n, int64_t lda, const 
                    &ro));
   *res_out = ro.res;
   return LYAP_OK;
+}
+
+int lyap_trace_loss(lyap_ctx_t* C, const double* Z, int64_t n, int64_t ldz, int64_t r, const double* D,
+                    const double* Cm, int64_t ldc, int64_t q, double* loss, double* dC, int64_t lddc) {
+  if (!C || !Z || !Cm || !loss || n <= 0 || r < 0 || q <= 0 || ldz < n || ldc < q || (dC && lddc < q))
+    return LYAP_ERR_ARG;
+  Ctx& X = *C;
+  LYAP_TRY(ensure(X.scal, 4096));
+  const int64_t rr = std::max<int64_t>(r, 1);
+  LYAP_TRY(ensure(X.tl, (size_t)2 * q * rr * 8 + 64));
+  double* Tm = P<double>(X.tl);
+  double* TD = Tm + (size_t)q * rr;
+  double* out = P<double>(X.scal) + 320;
+  if (r == 0) {
+    LYAP_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double), X.s));
+    if (dC) LYAP_TRY(set_zero<double>(dC, q, n, lddc, X.s));
+  } else {
+    LYAP_TRY(gemm<double>('N', 'N', q, r, n, 1.0, Cm, ldc, Z, ldz, 0.0, Tm, q, X.s));
+    trace_loss_kernel<<<1, 256, 0, X.s>>>(Tm, (int)q, (int)r, D, TD, out);
+    LYAP_CUDA_TRY(cudaGetLastError());
+    lyap_count_launch();
+    if (dC) LYAP_TRY(gemm<double>('N', 'T', q, n, r, 2.0, TD, q, Z, ldz, 0.0, dC, lddc, X.s));
+  }
+  return sync_read(X, out, loss, sizeof(double));
 }
 
 }  // extern "C"

@@ -320,11 +320,11 @@ static int* status_word() {
 
 static int launch_tc(int mode, int prec, const CUtensorMap& a, const CUtensorMap& b, int M, int N, int K,
                      const EpiGJ& eg, const EpiProd& ep, cudaStream_t s) {
-  static std::atomic<bool> attr{false};
-  if (!attr.load()) {
+  static DeviceOnce attr;
+  if (attr.need()) {
     LYAP_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
     LYAP_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-    attr.store(true);
+    attr.set();
   }
   int* st = status_word();
   if (!st) return LYAP_ERR_NOMEM;

@@ -90,6 +90,7 @@ SIGNATURES = {
     "lyap_adjoint": (C.c_int, [_P, _P, _I64, _I64, _P, _I64, _I64, _P, _I64, _P, _I64, _I64, _P, _P, _I64, _I64,
                                C.POINTER(LyapOpts), _P, _I64, _P, _I64, _P, _I64, _P, _I64, _I64, C.POINTER(_I64),
                                C.POINTER(LyapInfo)]),
+    "lyap_trace_loss": (C.c_int, [_P, _P, _I64, _I64, _I64, _P, _P, _I64, _I64, C.POINTER(_D), _P, _I64]),
     "lyap_rank_trunc": (C.c_int, [_P, _P, _I64, _I64, _I64, _D, C.POINTER(_I64)]),
     "lyap_sym_eig": (C.c_int, [_P, _P, _I64, _I64, _P, _P, _I64, C.c_int]),
     "lyap_last_error": (C.c_char_p, []),
@@ -289,21 +290,37 @@ def adjoint(A, L, Z, Cm, S=None, D=None, opts=None, want=("dA", "dL", "dS"), fac
     return {"dA": dA, "dL": dL, "dS": dS, "Zy": Zy[:, : ry.value] if Zy is not None else None, "info": info}
 
 
+def trace_loss_value(Z, Cm, D=None, want_grad=False):
+    """l = trace(C X C^T) for X = Z diag(D) Z^T, and dl/dC = 2 C X when want_grad
+    (lyap_trace_loss).  Returns (loss, dC or None)."""
+    ctx = context()
+    Z, Cm = _cm(Z), _cm(Cm)
+    n, r = Z.shape
+    q = Cm.shape[0]
+    Dd = D.contiguous() if D is not None else None
+    dC = cm_empty(q, n, Z.device) if want_grad else None
+    out = _D(0.0)
+    _check(ctx.lib.lyap_trace_loss(ctx.h, _P(Z.data_ptr()), n, n, r, _P(Dd.data_ptr()) if Dd is not None else None,
+                                   _P(Cm.data_ptr()), q, q, C.byref(out), _P(dC.data_ptr()) if dC is not None else None,
+                                   q), allow_warn=False)
+    return out.value, dC
+
+
 class LyapTraceLoss(torch.autograd.Function):
     """l = trace(C X C^T) for the solution X = Z diag(D) Z^T of A X + X A^T + L S L^T = 0
-    (lyap_solve_ir forward; S = None: W = L L^T).  backward: dA, dL, dS from lyap_adjoint
-    (which replays the forward inverse sequence transposed), dC = 2 C X."""
+    (lyap_solve_ir forward; S = None: W = L L^T; the loss itself by lyap_trace_loss).
+    backward: dA, dL, dS from lyap_adjoint (which replays the forward inverse sequence
+    transposed) and dC = 2 C X from lyap_trace_loss."""
 
     @staticmethod
     def forward(fctx, A, L, Cm, S=None, opts=None):
         Z, D, info = solve_ir(A, L, S, opts=opts)
-        CZ = Cm @ Z
-        loss = (CZ * CZ * D[None, :]).sum() if D is not None else (CZ * CZ).sum()
+        loss, _ = trace_loss_value(Z, Cm, D)
         fctx.opts = opts
         fctx.info = info
         fctx.save_for_backward(A, L, Cm, S if S is not None else torch.empty(0, device=A.device), Z,
                                D if D is not None else torch.empty(0, device=A.device))
-        return loss
+        return torch.tensor(loss, dtype=torch.float64, device=A.device)
 
     @staticmethod
     def backward(fctx, g):
@@ -311,8 +328,7 @@ class LyapTraceLoss(torch.autograd.Function):
         S = S if S.numel() else None
         D = D if D.numel() else None
         out = adjoint(A, L, Z, Cm, S=S, D=D, opts=fctx.opts)
-        ZD = Z * D[None, :] if D is not None else Z
-        dC = 2.0 * (Cm @ ZD) @ Z.T
+        _, dC = trace_loss_value(Z, Cm, D, want_grad=True)
         dS = g * out["dS"] if S is not None else None
         return g * out["dA"], g * out["dL"], g * dC, dS, None
 
@@ -405,4 +421,5 @@ lyap_invert_noalloc = invert_noalloc
 lyap_adjoint = adjoint
 lyap_solve_ir_batched = solve_ir_batched
 lyap_rank_trunc = rank_trunc
+lyap_trace_loss = trace_loss_value
 lyap_sym_eig = sym_eig

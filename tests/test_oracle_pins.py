@@ -344,6 +344,29 @@ def test_residual_eq41_zero_at_solution():
     assert O.residual_eq41(A, Z, W) < 1e-14
 
 
+def test_residual_eq41_normalisation_closed_form():
+    # Eq. (4.1) at X = c X*, with X* the exact solution: A X + X A^T + W = (1 - c) W, so the
+    # relative residual is |1 - c| ||W||_F / (||W||_F + 2 c ||X*||_F ||A||_F).  For
+    # A = diag(-1, -2), L = (1, 1)^T the pieces are worked out by hand: W = [[1, 1], [1, 1]]
+    # (||W||_F = 2), X*_ij = 1 / (i + j) over i, j in {1, 2} = [[1/2, 1/3], [1/3, 1/4]]
+    # (||X*||_F = sqrt(77) / 12), ||A||_F = sqrt(5).  At c = 2 the value is
+    # 2 / (2 + 4 sqrt(77) sqrt(5) / 12) = 6 / (6 + sqrt(385)); at c = 1/2 it is
+    # 1 / (2 + sqrt(385) / 12) = 12 / (24 + sqrt(385)).  A wrong factor 2, a missing
+    # ||W||_F term, or a 2-norm in place of a Frobenius norm changes both values.
+    A = np.diag([-1.0, -2.0])
+    L = np.array([[1.0], [1.0]])
+    W = L @ L.T
+    Xs = np.array([[0.5, 1.0 / 3.0], [1.0 / 3.0, 0.25]])
+    C = np.linalg.cholesky(Xs)
+    for c, want in ((2.0, 6.0 / (6.0 + math.sqrt(385.0))), (0.5, 12.0 / (24.0 + math.sqrt(385.0)))):
+        Z = math.sqrt(c) * C
+        assert abs(O.residual_eq41(A, Z, W) - want) <= 1e-15 * want
+        # the LDL^T form (X = Z diag(y) Z^T) with y = c on the Cholesky factor of X*
+        assert abs(O.residual_eq41(A, C, W, np.full(2, c)) - want) <= 1e-15 * want
+    # Z = 0: the residual is W itself and the normalisation reduces to ||W||_F
+    assert O.residual_eq41(A, np.zeros((2, 1)), W) == 1.0
+
+
 # ------------------------------------------------------- refinement algorithms
 
 @pytest.mark.parametrize("us", ["fp64", "fp32", "fp16", "bf16"])
