@@ -80,7 +80,15 @@ typedef struct {
   int stag_count;       /* consecutive stagnating steps that stop IR (2) */
   int project_psd;      /* 1: PSD projection in the solution update (forced off for indefinite S) */
   int profile;          /* 1: record per-phase device times into lyap_info_t.phase_ms (CUDA events) */
-  int reserved[7];
+  int ckpt_every;       /* 0: the context keeps every inverse A_k^{-1} of the first solve (Sec. 3.4);
+                           c > 0: it keeps only the iterates A_0, A_c, A_2c, ... (working
+                           precision) and every later solve (corrections, adjoint) recomputes the
+                           inverses from them with the recorded mu_k: one inversion per replayed
+                           step in exchange for ceil(K / c) instead of K stored n x n matrices */
+  int64_t mem_budget;   /* bytes the stored inverse sequence may take (0 = no limit); when kmax
+                           stored inverses would exceed it, checkpoints every ckpt_every steps
+                           (4 when ckpt_every = 0) are kept instead */
+  int reserved[4];
 } lyap_opts_t;
 
 /* Phases reported in lyap_info_t.phase_ms / phase_calls / phase_flops when

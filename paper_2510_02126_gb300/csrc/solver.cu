@@ -91,6 +91,14 @@ struct lyap_ctx {
   size_t store_elt = 0;
   int64_t store_ld = 0;    // row pitch (elements) of a stored inverse
   int64_t store_rows = 0;  // rows allocated per stored inverse
+  // checkpointed sequence (opts.ckpt_every / opts.mem_budget): the store holds the Newton
+  // iterates A_0, A_c, A_2c, ... (working precision, row-major n x n) instead of the
+  // inverses; every use recomputes the inverses of a segment from its checkpoint, using
+  // the recorded mu_k and storage exponents, into the one-slot buffer inv1
+  int store_ckpt = 0;       // 0: inverses stored; c > 0: checkpoint every c steps
+  size_t store_welt = 0;    // element size of a checkpoint (working precision)
+  lyap::Buf inv1;           // the inverse of the current step (checkpoint mode)
+  int64_t recomputed = 0;   // inversions recomputed from checkpoints by the current call
   // FP64 refinement buffers
   lyap::Buf F, tau, Tm, TP, H, w, Qh, Csel, Lp, Lm, Zs, Zbest, G, gram, ysol, ybest, ytmp, Lw, Sd, Vs, Lst, Rtau, Bm, VB;
   // scratch of the QR and eigen kernels
@@ -184,6 +192,14 @@ __global__ void newton_mu_kernel(NewtonState* st, int n, int scaling, int store1
   if (!isfinite(mu) || !(mu > 0.0) || !isfinite(st->ssX)) atomicCAS(&st->status, 0, LYAP_ERR_NONFINITE);
   st->mu = mu;
   st->eX = store16 ? pow2_exponent(st->maxX) : 0;
+}
+
+// mu_k and the storage exponent of A_k^{-1} as recorded by the first solve (recomputation
+// of an inverse from a checkpoint reproduces the recorded sequence)
+__global__ void newton_recorded_mu_kernel(NewtonState* st, const double* __restrict__ dmu, const int* __restrict__ dex,
+                                          int kk) {
+  st->mu = dmu[kk];
+  st->eX = dex[kk];
 }
 
 // A_{k+1} = (mu A_k + mu^{-1} A_k^{-1}) / 2 with A_k^{-1}[i, j] = X[i, pinv[j]];
@@ -641,15 +657,28 @@ static int transpose_store(Ctx& C) {
   if (C.store_count == 0) return LYAP_OK;
   const int n = C.store_n;
   const unsigned nt = (unsigned)ceil_div(n, 32);
-  dim3 grid(nt, nt, (unsigned)C.store_count), block(32, 8);
-  const size_t slot = (size_t)C.store_rows * C.store_ld;
-  if (C.store_elt == 2) transpose_slots_kernel<uint16_t><<<grid, block, 0, C.s>>>((uint16_t*)C.store.p, n, C.store_ld, slot);
-  else if (C.store_elt == 4) transpose_slots_kernel<uint32_t><<<grid, block, 0, C.s>>>((uint32_t*)C.store.p, n, C.store_ld, slot);
-  else transpose_slots_kernel<uint64_t><<<grid, block, 0, C.s>>>((uint64_t*)C.store.p, n, C.store_ld, slot);
+  // checkpoint mode: the iterates are transposed (A_k -> A_k^T); the inverses recomputed
+  // from them are then those of A_k^T = (A_k^{-1})^T
+  const int count = C.store_ckpt ? (int)ceil_div(C.store_count, C.store_ckpt) : C.store_count;
+  const int64_t ld = C.store_ckpt ? n : C.store_ld;
+  const size_t slot = C.store_ckpt ? (size_t)n * n : (size_t)C.store_rows * C.store_ld;
+  const size_t elt = C.store_ckpt ? C.store_welt : C.store_elt;
+  dim3 grid(nt, nt, (unsigned)count), block(32, 8);
+  if (elt == 2) transpose_slots_kernel<uint16_t><<<grid, block, 0, C.s>>>((uint16_t*)C.store.p, n, ld, slot);
+  else if (elt == 4) transpose_slots_kernel<uint32_t><<<grid, block, 0, C.s>>>((uint32_t*)C.store.p, n, ld, slot);
+  else transpose_slots_kernel<uint64_t><<<grid, block, 0, C.s>>>((uint64_t*)C.store.p, n, ld, slot);
   LYAP_CUDA_TRY(cudaGetLastError());
   lyap_count_launch();
   return LYAP_OK;
 }
+
+// Slot of the inverse used at Newton step kk: the stored one, or the recomputed one.
+static void* inv_slot(Ctx& C, int kk) {
+  if (C.store_ckpt) return C.inv1.p;
+  return (char*)C.store.p + (size_t)kk * (size_t)C.store_rows * C.store_ld * C.store_elt;
+}
+// Checkpoint j (iterate A_{j c}) in checkpoint mode.
+static void* ckpt_slot(Ctx& C, int j) { return (char*)C.store.p + (size_t)j * C.store_n * C.store_n * C.store_welt; }
 
 // ---------------------------------------------------------------------------
 // the inversion (K1-K3) on the current Newton iterate
@@ -672,12 +701,12 @@ static int invert_current(Ctx& C, const T* Acur, int n, int prec) {
 template <typename T>
 static int factor_product(Ctx& C, int n, int c, int prec, int kk, T* Z) {
   if (is16(prec)) {
-    const void* Xs = (const char*)C.store.p + (size_t)kk * (size_t)C.store_rows * C.store_ld * C.store_elt;
+    const void* Xs = inv_slot(C, kk);
     LYAP_TRY(factor_to_16(prec, (const float*)Z, n, c, n, C.Zh.p, P<int>(C.eZ), C.s));
     LYAP_TRY(tc_product(prec, n, c, Xs, P<int>(C.dex) + kk, C.Zh.p, P<int>(C.eZ), (float*)Z + (size_t)c * n, n,
                         C.s));
   } else {
-    const T* Xs = (const T*)((const char*)C.store.p + (size_t)kk * (size_t)C.store_rows * C.store_ld * C.store_elt);
+    const T* Xs = (const T*)inv_slot(C, kk);
     // Xs is row-major, i.e. the transpose of a column-major n x n matrix
     LYAP_TRY(gemm<T>('T', 'N', n, c, n, T(1), Xs, n, Z, n, T(0), Z + (size_t)c * n, n, C.s));
   }
@@ -774,26 +803,41 @@ static int newton_run(Ctx& C, int n, int c0, bool ldlt, const NewtonOpts& o, boo
   T* Acur = P<T>(C.A0);
   T* Anext = P<T>(C.A1);
   bool finished = false;
+  const int ce = C.store_ckpt;
+  if (!compute && ce) LYAP_CUDA_TRY(cudaMemsetAsync(C.gj.status, 0, sizeof(int), C.s));
   for (int kk = 0; kk < K; ++kk) {
-    if (compute) {
+    // the inverse of step kk: computed (first solve), or recomputed from the last checkpoint
+    // with the recorded mu_kk and storage exponent (checkpoint mode); a plain replay reads it
+    // from the store
+    if (compute || ce) {
       if (kk >= 64) {
         lyap_set_error_message("more than 64 Newton steps", __FILE__, __LINE__);
         return LYAP_ERR_NOCONV;
       }
-      LYAP_CUDA_TRY(cudaMemsetAsync(C.gj.status, 0, sizeof(int), C.s));
+      if (ce && kk % ce == 0) {
+        void* cp = ckpt_slot(C, kk / ce);
+        if (compute) LYAP_CUDA_TRY(cudaMemcpyAsync(cp, Acur, sizeof(T) * nn, cudaMemcpyDeviceToDevice, C.s));
+        else LYAP_CUDA_TRY(cudaMemcpyAsync(Acur, cp, sizeof(T) * nn, cudaMemcpyDeviceToDevice, C.s));
+      }
+      if (compute) LYAP_CUDA_TRY(cudaMemsetAsync(C.gj.status, 0, sizeof(int), C.s));
       mark(C, LYAP_PHASE_INVERT);
       LYAP_TRY(invert_current<T>(C, Acur, n, o.prec));
+      if (!compute) C.recomputed += 1;
       mark(C, LYAP_PHASE_NEWTON);
       const T* X = (const T*)C.gj.M[C.gj.cur];
       const int* perm = C.gj.perm[C.gj.cur];
       pinv_kernel<<<nblk(n), 256, 0, C.s>>>(perm, P<int>(C.pinv), n);
       lyap_count_launch();
-      LYAP_TRY(sumsq<T>(X, n, n, n, &st->ssX, P<double>(C.part), C.s));
-      LYAP_TRY(maxabs<T>(X, n, n, n, &st->maxX, P<double>(C.part), C.s));
-      if (o.scaling == LYAP_SCALE_DET) LYAP_TRY(pivot_logs(C.gj, &st->logdet, C.s));
-      newton_mu_kernel<<<1, 1, 0, C.s>>>(st, n, o.scaling, is16(o.prec) ? 1 : 0);
+      if (compute) {
+        LYAP_TRY(sumsq<T>(X, n, n, n, &st->ssX, P<double>(C.part), C.s));
+        LYAP_TRY(maxabs<T>(X, n, n, n, &st->maxX, P<double>(C.part), C.s));
+        if (o.scaling == LYAP_SCALE_DET) LYAP_TRY(pivot_logs(C.gj, &st->logdet, C.s));
+        newton_mu_kernel<<<1, 1, 0, C.s>>>(st, n, o.scaling, is16(o.prec) ? 1 : 0);
+      } else {
+        newton_recorded_mu_kernel<<<1, 1, 0, C.s>>>(st, P<double>(C.dmu), P<int>(C.dex), kk);
+      }
       lyap_count_launch();
-      void* slot = (char*)C.store.p + (size_t)kk * (size_t)C.store_rows * C.store_ld * C.store_elt;
+      void* slot = inv_slot(C, kk);
       const unsigned nb = RED_BLOCKS;
       switch (o.prec) {
         case LYAP_FP64:
@@ -818,18 +862,21 @@ static int newton_run(Ctx& C, int n, int c0, bool ldlt, const NewtonOpts& o, boo
           break;
       }
       LYAP_CUDA_TRY(cudaGetLastError());
-      newton_sums_kernel<<<1, 96, 0, C.s>>>(P<double>(C.part), nb, st);
-      lyap_count_launch(2);
-      if (!o.norm_fro) {
-        colsum_kernel<T><<<nblk(n, 128), 128, 0, C.s>>>(n, Anext, P<double>(C.colsum));
-        lyap_count_launch();
-        LYAP_TRY(maxabs<double>(P<double>(C.colsum), n, 1, n, &st->stopv, P<double>(C.part) + 3 * RED_BLOCKS, C.s));
-      }
-      newton_test_kernel<<<1, 1, 0, C.s>>>(st, o.tau, o.norm_fro, o.stop_after, o.delta_rule, o.scale_off,
-                                           P<double>(C.dmu), P<int>(C.dex), kk);
       lyap_count_launch();
+      if (compute) {
+        newton_sums_kernel<<<1, 96, 0, C.s>>>(P<double>(C.part), nb, st);
+        lyap_count_launch();
+        if (!o.norm_fro) {
+          colsum_kernel<T><<<nblk(n, 128), 128, 0, C.s>>>(n, Anext, P<double>(C.colsum));
+          lyap_count_launch();
+          LYAP_TRY(maxabs<double>(P<double>(C.colsum), n, 1, n, &st->stopv, P<double>(C.part) + 3 * RED_BLOCKS, C.s));
+        }
+        newton_test_kernel<<<1, 1, 0, C.s>>>(st, o.tau, o.norm_fro, o.stop_after, o.delta_rule, o.scale_off,
+                                             P<double>(C.dmu), P<int>(C.dex), kk);
+        lyap_count_launch();
+        C.store_count = kk + 1;
+      }
       std::swap(Acur, Anext);
-      C.store_count = kk + 1;
     }
     // factor update with the stored A_kk^{-1}
     if (2 * c + 8 > 2 * n + 8) {
@@ -883,6 +930,11 @@ static int newton_run(Ctx& C, int n, int c0, bool ldlt, const NewtonOpts& o, boo
     int qrs = 0;
     LYAP_TRY(sync_read(C, C.qr.status, &qrs, sizeof(int)));
     if (qrs) return qrs;
+    if (ce) {
+      int gjs = 0;
+      LYAP_TRY(sync_read(C, C.gj.status, &gjs, sizeof(int)));
+      if (gjs) return gjs;
+    }
   }
   *c_out = c;
   return LYAP_OK;
@@ -979,7 +1031,7 @@ int lyap_ctx_destroy(lyap_ctx_t* C) {
                 &C->Lm, &C->Zs, &C->Zbest, &C->G, &C->gram, &C->ysol, &C->ybest, &C->ytmp, &C->Lw, &C->Sd,
                 &C->Vs, &C->Lst, &C->Rtau, &C->Bm, &C->VB, &C->qrBar, &C->qrStatus, &C->qrCand, &C->qrNorms, &C->qrPiv, &C->qrRdiag, &C->qrWork,
                 &C->qrRank, &C->eigWork32, &C->eigX, &C->eigR, &C->eigS, &C->eigHX, &C->eigE, &C->eigLam,
-                &C->eigRed, &C->eigW, &C->eigPv, &C->eigInt, &C->At, &C->Ct, &C->ZY, &C->adjT, &C->Hf, &C->tl};
+                &C->eigRed, &C->eigW, &C->eigPv, &C->eigInt, &C->At, &C->Ct, &C->ZY, &C->adjT, &C->Hf, &C->tl, &C->inv1};
   for (Buf* b : all) free_buf(*b);
   for (lyap_ctx* w : C->pool) lyap_ctx_destroy(w);
   for (cudaStream_t st : C->pool_streams) cudaStreamDestroy(st);
@@ -1133,9 +1185,22 @@ static int newton_solve(Ctx& C, const Problem& pb, const double* Lr, int mr, con
     // 16-bit inverses are tensor-core A operands: row pitch and row count follow tc_kpitch / tc_rows
     C.store_ld = (selt == 2) ? tc_kpitch(n) : n;
     C.store_rows = (selt == 2) ? tc_rows(n) : n;
-    LYAP_TRY(ensure(C.store, (size_t)no.kmax * (size_t)C.store_rows * C.store_ld * selt));
-    if (selt == 2 && (C.store_ld != n || C.store_rows != n))  // K padding must read as zero
-      LYAP_CUDA_TRY(cudaMemsetAsync(C.store.p, 0, (size_t)no.kmax * C.store_rows * C.store_ld * selt, C.s));
+    const size_t inv_bytes = (size_t)C.store_rows * C.store_ld * selt;
+    const bool padded = selt == 2 && (C.store_ld != n || C.store_rows != n);  // K padding must read as zero
+    // checkpoints every ckpt_every steps when asked, or (every 4 steps) when the full
+    // sequence of kmax inverses would exceed mem_budget
+    int ce = o.ckpt_every > 0 ? o.ckpt_every : 0;
+    if (ce == 0 && o.mem_budget > 0 && (double)no.kmax * (double)inv_bytes > (double)o.mem_budget) ce = 4;
+    C.store_ckpt = ce;
+    C.store_welt = sizeof(T);
+    if (ce) {
+      LYAP_TRY(ensure(C.store, (size_t)ceil_div(no.kmax, ce) * nn * sizeof(T)));
+      LYAP_TRY(ensure(C.inv1, inv_bytes));
+      if (padded) LYAP_CUDA_TRY(cudaMemsetAsync(C.inv1.p, 0, inv_bytes, C.s));
+    } else {
+      LYAP_TRY(ensure(C.store, (size_t)no.kmax * inv_bytes));
+      if (padded) LYAP_CUDA_TRY(cudaMemsetAsync(C.store.p, 0, (size_t)no.kmax * inv_bytes, C.s));
+    }
     C.store_elt = selt;
     C.store_n = n;
     C.store_prec = o.u_s;
@@ -1572,6 +1637,8 @@ static int solve_common(Ctx& C, const Problem& pb, const lyap_opts_t& o, bool re
   *rank_out = best_c;
   info->rank = best_c;
   info->res_final = best;
+  info->n_inversions += (int)C.recomputed;
+  C.recomputed = 0;
   return status;
 }
 
@@ -1588,6 +1655,7 @@ static int solve_entry(lyap_ctx_t* C, const double* A, int64_t n, int64_t lda, c
   const int64_t l0 = g_launches;
   C->profile = opts->profile != 0;
   C->marks_used = 0;
+  C->recomputed = 0;
   for (double& f : C->flops) f = 0.0;
   cudaEventRecord(C->e0, C->s);
   mark(*C, LYAP_PHASE_OTHER);
@@ -1626,6 +1694,7 @@ static int adjoint_entry(lyap_ctx_t* Cp, const double* A, int64_t n, int64_t lda
   const int64_t l0 = g_launches;
   C.profile = opts->profile != 0;
   C.marks_used = 0;
+  C.recomputed = 0;
   for (double& f : C.flops) f = 0.0;
   cudaEventRecord(C.e0, C.s);
   mark(C, LYAP_PHASE_OTHER);

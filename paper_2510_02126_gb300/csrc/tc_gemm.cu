@@ -19,9 +19,15 @@
 
 namespace lyap {
 
-constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 4;
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64;
 constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 2;  // 16 KB per operand per stage
-constexpr int TC_SMEM = TC_STAGES * 2 * TC_TILE_BYTES + 1024 + 256;
+// Stages of the TMA ring: the Gauss-Jordan update has K = 64 (one stage suffices, and the
+// small footprint lets four CTAs share an SM -- the TMEM limit -- so that one CTA's
+// epilogue overlaps another's loads); the factor product streams K = n through four.
+__host__ __device__ constexpr int tc_stages(int mode) { return mode == 0 ? 1 : 4; }
+__host__ __device__ constexpr int tc_smem(int mode) { return tc_stages(mode) * 2 * TC_TILE_BYTES + 1024 + 256; }
+// epilogue staging of the update (per warp 32 x 33 floats) fits in the stage buffers
+static_assert(4 * 32 * 33 * 4 <= 2 * TC_TILE_BYTES, "staging area");
 
 // ---------------------------------------------------------------------------
 // PTX wrappers
@@ -131,6 +137,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = base;
+  constexpr int TC_STAGES = tc_stages(MODE);
   unsigned char* sB = base + TC_STAGES * TC_TILE_BYTES;
   uint64_t* full = reinterpret_cast<uint64_t*>(base + 2 * TC_STAGES * TC_TILE_BYTES);
   uint64_t* done = full + TC_STAGES;
@@ -205,18 +212,28 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const int row = m0 + warp * 32 + lane;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
     if (MODE == 0) {
+      // TMEM rows are thread-private (lane = row), global rows are 4 n bytes apart: each
+      // warp stages 32 x 32 blocks through shared memory (the drained stage buffers) so that
+      // every global load and store covers 32 consecutive columns of one row
       const float sc = ldexpf(1.f, eg.exps[2 * eg.step] + eg.exps[2 * eg.step + 1]);
-      const bool rv = row < eg.n;
-      const float* src = rv ? eg.Mcur + (size_t)eg.orig[row] * eg.n : nullptr;
-      float* dst = rv ? eg.Mnew + (size_t)row * eg.n : nullptr;
-      for (int j0 = 0; j0 < TC_BN; j0 += 16) {
-        float v[16];
+      float* stg = reinterpret_cast<float*>(base) + warp * 32 * 33;
+      const int rbase = m0 + warp * 32;
+      const int my_src = (rbase + lane < eg.n) ? eg.orig[rbase + lane] : 0;
+      for (int j0 = 0; j0 < TC_BN; j0 += 32) {
+        float v[32];
         tmem_ld16(trow + j0, v);
-        if (!rv) continue;
+        tmem_ld16(trow + j0 + 16, v + 16);
+        __syncwarp();
 #pragma unroll
-        for (int t = 0; t < 16; ++t) {
-          const int x = n0 + j0 + t;
-          if (x < eg.n && (x < eg.k || x >= eg.k + eg.bb)) dst[x] = src[x] + sc * v[t];
+        for (int t = 0; t < 32; ++t) stg[lane * 33 + t] = v[t];
+        __syncwarp();
+        const int x = n0 + j0 + lane;
+        const bool xok = x < eg.n && (x < eg.k || x >= eg.k + eg.bb);
+#pragma unroll 4
+        for (int rr = 0; rr < 32; ++rr) {
+          const int src = __shfl_sync(0xffffffffu, my_src, rr);
+          if (rbase + rr < eg.n && xok)
+            eg.Mnew[(size_t)(rbase + rr) * eg.n + x] = eg.Mcur[(size_t)src * eg.n + x] + sc * stg[rr * 33 + lane];
         }
       }
     } else {
@@ -322,16 +339,16 @@ static int launch_tc(int mode, int prec, const CUtensorMap& a, const CUtensorMap
                      const EpiGJ& eg, const EpiProd& ep, cudaStream_t s) {
   static DeviceOnce attr;
   if (attr.need()) {
-    LYAP_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-    LYAP_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    LYAP_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(0)));
+    LYAP_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(1)));
     attr.set();
   }
   int* st = status_word();
   if (!st) return LYAP_ERR_NOMEM;
   dim3 grid((unsigned)ceil_div(N, TC_BN), (unsigned)ceil_div(M, TC_BM));
   const int fmt = (prec == LYAP_BF16) ? 1 : 0;
-  if (mode == 0) tc_gemm_kernel<0><<<grid, 128, TC_SMEM, s>>>(a, b, M, N, K, fmt, eg, ep, st);
-  else tc_gemm_kernel<1><<<grid, 128, TC_SMEM, s>>>(a, b, M, N, K, fmt, eg, ep, st);
+  if (mode == 0) tc_gemm_kernel<0><<<grid, 128, tc_smem(0), s>>>(a, b, M, N, K, fmt, eg, ep, st);
+  else tc_gemm_kernel<1><<<grid, 128, tc_smem(1), s>>>(a, b, M, N, K, fmt, eg, ep, st);
   LYAP_CUDA_TRY(cudaGetLastError());
   lyap_count_launch();
   return LYAP_OK;

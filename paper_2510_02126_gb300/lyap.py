@@ -35,7 +35,7 @@ class LyapOpts(C.Structure):
         ("stop_after", C.c_int), ("delta_rule", C.c_int), ("scale_off", C.c_double), ("rank_tol", C.c_double),
         ("rho", C.c_double), ("kmax", C.c_int), ("imax", C.c_int), ("tau_ir", C.c_double), ("eta_r", C.c_double),
         ("eta_s", C.c_double), ("stag_theta", C.c_double), ("stag_count", C.c_int), ("project_psd", C.c_int),
-        ("profile", C.c_int), ("reserved", C.c_int * 7),
+        ("profile", C.c_int), ("ckpt_every", C.c_int), ("mem_budget", C.c_int64), ("reserved", C.c_int * 4),
     ]
 
 

@@ -43,3 +43,30 @@ def test_opts_default_without_gpu():
     from paper_2510_02126_gb300 import lyap as liblyap
     o = liblyap.make_opts()
     assert o.rho == 0.1 and o.imax == 50 and o.kmax == 50 and o.eta_r == 1e-4 and o.stop_after == 2
+
+
+def test_field_offsets_match_c_compiler(tmp_path):
+    # every field of the option and info structs sits where the C compiler puts it
+    import shutil
+    import subprocess
+    import pytest
+    from paper_2510_02126_gb300 import lyap as liblyap
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "liblyap.h"', "int main(void) {"]
+    for cname, st in (("lyap_opts_t", liblyap.LyapOpts), ("lyap_info_t", liblyap.LyapInfo)):
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in st._fields_:
+            lines.append(f'  printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                          check=True).stdout.split("\n") if l)
+    for cname, st in (("lyap_opts_t", liblyap.LyapOpts), ("lyap_info_t", liblyap.LyapInfo)):
+        assert int(out[cname]) == ctypes.sizeof(st), cname
+        for f, _ in st._fields_:
+            assert int(out[f"{cname}.{f}"]) == getattr(st, f).offset, (cname, f)

@@ -134,3 +134,52 @@ def test_adjoint_zero_loss_matrix():
     Z, _, _ = lp.solve_ir(T(d["A"]), T(d["L"]), opts=o)
     out = lp.adjoint(T(d["A"]), T(d["L"]), Z, torch.zeros((2, 40), dtype=torch.float64, device="cuda"), opts=o)
     assert float(out["dA"].abs().max()) == 0.0 and float(out["dL"].abs().max()) == 0.0
+
+
+# ------------------------------------------------------- checkpointed inverse sequence
+
+def test_checkpointed_sequence_equals_stored():
+    # ckpt_every = 4: the context keeps A_0, A_4, ... and every correction solve recomputes
+    # the inverses with the recorded mu_k -- the same numbers as the stored sequence
+    lp = lib()
+    d = gen.paper_synthetic(300, 1.5)
+    A, L = T(d["A"]), T(d["L"])
+    Z0, _, i0 = lp.solve_ir(A, L, u_s="fp16", tau_ir=1e-12)
+    Z1, _, i1 = lp.solve_ir(A, L, u_s="fp16", tau_ir=1e-12, ckpt_every=4)
+    assert i0.converged and i1.converged
+    assert (i1.ir_steps, i1.newton_total, i1.rank) == (i0.ir_steps, i0.newton_total, i0.rank)
+    assert i0.n_inversions == i0.newton_max          # stored: inverted once, replayed
+    assert i1.n_inversions == i1.newton_total        # checkpoints: every replayed step inverts
+    assert relF(N(Z1) @ N(Z1).T, N(Z0) @ N(Z0).T) <= 1e-13
+    # a memory budget below kmax stored inverses selects the checkpoints by itself
+    Z2, _, i2 = lp.solve_ir(A, L, u_s="fp16", tau_ir=1e-12, mem_budget=1 << 20)
+    assert i2.n_inversions == i2.newton_total
+    assert relF(N(Z2) @ N(Z2).T, N(Z0) @ N(Z0).T) <= 1e-13
+
+
+@pytest.mark.parametrize("n", [256, 2048])
+def test_adjoint_checkpointed_equals_stored(n):
+    # the adjoint replays the forward sequence of A transposed: from stored inverses, or
+    # from checkpoints of A_k transposed (inverting A_k^T); the gradients agree
+    lp = lib()
+    d = gen.paper_synthetic(n, 1.0)
+    A, L = T(d["A"]), T(d["L"])
+    Cm = T(gen.rng(gen.SEED_BASE + 48).standard_normal((4, n)))
+    grads = []
+    for ck in (0, 4):
+        o = lp.make_opts(u_s="fp16", tau_ir=1e-13, imax=30, ckpt_every=ck)
+        Z, _, info = lp.solve_ir(A, L, opts=o)
+        assert info.converged
+        out = lp.adjoint(A, L, Z, Cm, opts=o)
+        assert out["info"].converged
+        if ck:
+            assert out["info"].n_inversions == out["info"].newton_total
+        else:
+            assert out["info"].n_inversions == 0
+        grads.append((N(out["dA"]), N(out["dL"])))
+    assert relF(grads[1][0], grads[0][0]) <= 1e-10
+    assert relF(grads[1][1], grads[0][1]) <= 1e-10
+    if n <= 256:
+        ref = O.adjoint(d["A"], d["L"], N(Cm))
+        assert relF(grads[1][0], ref["dA"]) <= 1e-9
+        assert relF(grads[1][1], ref["dL"]) <= 1e-9

@@ -241,8 +241,10 @@ def test_ir_stagnation_rule_on_gpu():
     assert info.res_final == min(hist)
     assert info.res_final <= 1e-14
     assert abs(O.residual_eq41(A, N(Z), W) - info.res_final) <= 1e-2 * info.res_final + 1e-17
-    # the oracle stagnates on the same input, at a residual of the same FP64 floor
+    # the oracle stagnates on the same input at the FP64 floor as well; the GPU's best
+    # residual is at least as small (its FP16 inner solves accumulate in FP32)
     Zo, oinfo = O.ir_chol(A, L, O.Opts(u_s="fp16", tau_ir=1e-30))
     assert oinfo.stagnated and not oinfo.converged
     assert _stagnation_stop(oinfo.res_hist) == len(oinfo.res_hist) - 1
-    assert 0.1 <= info.res_final / oinfo.res_final <= 10.0, (info.res_final, oinfo.res_final)
+    assert oinfo.res_final <= 1e-14
+    assert info.res_final <= 10.0 * oinfo.res_final, (info.res_final, oinfo.res_final)
