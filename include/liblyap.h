@@ -88,7 +88,10 @@ typedef struct {
   int64_t mem_budget;   /* bytes the stored inverse sequence may take (0 = no limit); when kmax
                            stored inverses would exceed it, checkpoints every ckpt_every steps
                            (4 when ckpt_every = 0) are kept instead */
-  int reserved[4];
+  int fp64_products;    /* FP64 matrix products of the refinement: 0 = library's choice (emulated
+                           on the FP16 tensor cores above a size threshold), 1 = FP64 SIMT,
+                           2 = always emulated (see lyap_dgemm) */
+  int reserved[3];
 } lyap_opts_t;
 
 /* Phases reported in lyap_info_t.phase_ms / phase_calls / phase_flops when
@@ -240,6 +243,24 @@ int lyap_residual(lyap_ctx_t* ctx, const double* A, int64_t n, int64_t lda,
  */
 int lyap_trace_loss(lyap_ctx_t* ctx, const double* Z, int64_t n, int64_t ldz, int64_t r, const double* D,
                     const double* Cm, int64_t ldc, int64_t q, double* loss, double* dC, int64_t lddc);
+
+/*
+ * FP64 matrix product C = alpha op(A) op(B) + beta C (op = 'N' or 'T'; column-major DEVICE
+ * operands, beta == 0 does not read C): the products of the FP64 steps of the method -- A Z and
+ * the core matrices T P T^T, Gamma J Gamma^T of Fragments ResFacChol / SolUptChol (Sec. 2.1),
+ * the Gram matrices of Eq. (4.1), the eigen-refinement products.
+ *   method 1: FP64 SIMT arithmetic.
+ *   method 2: emulated on the FP16 tensor cores (no counterpart in the paper): every row of
+ *             op(A) and column of op(B) is scaled by a power of two and cut into 8 digits of
+ *             7 bits; digit products are exact in the FP32 accumulators (K in chunks of 1024)
+ *             and the 36 leading pairs are summed in FP64.  Error about 2^-50 K max|a| max|b|
+ *             per entry (row / column maxima), the order of an FP64 product's bound.
+ *   method 0: 2 for products of at least 3e7 multiply-adds, 1 below.
+ * Synchronises the context stream; returns LYAP_ERR_TIMEOUT if a bounded device wait gave up.
+ */
+int lyap_dgemm(lyap_ctx_t* ctx, char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+               const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+               int method);
 
 /*
  * Dense inversion behind every Newton step (Sec. 3.3 cost model: 2 n^3 flops):

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(PKG, "liblyap.so")
-SOURCES = ["dense.cu", "qr.cu", "eig.cu", "gj_inverse.cu", "tc_gemm.cu", "solver.cu", "noalloc.cu"]
+SOURCES = ["dense.cu", "qr.cu", "eig.cu", "gj_inverse.cu", "tc_gemm.cu", "solver.cu", "noalloc.cu", "ozaki.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-diag-suppress", "177"]
 

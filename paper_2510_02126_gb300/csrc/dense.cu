@@ -1,4 +1,5 @@
 #include "dense.cuh"
+#include "ozaki.cuh"
 
 namespace lyap {
 
@@ -94,6 +95,26 @@ static int num_sms() {
   return g_num_sms;
 }
 
+static thread_local int g_dgemm_method = DGEMM_AUTO;
+void set_dgemm_method(int method) { g_dgemm_method = method; }
+int dgemm_method() { return g_dgemm_method; }
+
+// FP64 products large enough for the tensor-core emulation (or forced to it)
+static bool use_tensor_fp64(int64_t M, int64_t N, int64_t K) {
+  if (g_dgemm_method == DGEMM_SIMT) return false;
+  if (g_dgemm_method == DGEMM_TENSOR) return true;
+  return (double)M * (double)N * (double)K >= OZ_MIN_MACS;
+}
+
+// C[j, i] = C[i, j] for i < j (the upper triangle of a symmetric product is the result)
+__global__ void mirror_upper_kernel(double* __restrict__ C, int64_t N, int64_t ldc) {
+  const int64_t total = N * N;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / N, i = e - j * N;
+    if (i > j) C[i + j * ldc] = C[j + i * ldc];
+  }
+}
+
 template <typename T, int TILE>
 static void gemm_launch(bool TA, bool TB, int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t lda,
                         const T* B, int64_t ldb, T beta, T* C, int64_t ldc, cudaStream_t s) {
@@ -111,6 +132,9 @@ int gemm(char ta, char tb, int64_t M, int64_t N, int64_t K, T alpha, const T* A,
   if (K <= 0) {
     if (beta == T(0)) return set_zero<T>(C, M, N, ldc, s);
     return scale_cols<T>(C, M, N, ldc, nullptr, s);  // beta must be 0 or 1 here
+  }
+  if constexpr (sizeof(T) == 8) {
+    if (use_tensor_fp64(M, N, K)) return ozaki_dgemm(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
   }
   const bool TA = (ta == 'T' || ta == 't'), TB = (tb == 'T' || tb == 't');
   // 64-wide tiles when they already give every SM two tiles, 32-wide tiles otherwise
@@ -130,6 +154,16 @@ int gemm_sym(char ta, char tb, int64_t N, int64_t K, T alpha, const T* A, int64_
              T beta, T* C, int64_t ldc, cudaStream_t s) {
   if (N <= 0) return LYAP_OK;
   if (K <= 0) return gemm<T>(ta, tb, N, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
+  if constexpr (sizeof(T) == 8) {
+    if (use_tensor_fp64(N, N, K)) {
+      // the full product, then its upper triangle mirrored (exact symmetry, as below)
+      LYAP_TRY(ozaki_dgemm(ta, tb, N, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s));
+      mirror_upper_kernel<<<(unsigned)std::min<int64_t>(4096, ceil_div(N * N, 256)), 256, 0, s>>>(C, N, ldc);
+      LYAP_CUDA_TRY(cudaGetLastError());
+      lyap_count_launch();
+      return LYAP_OK;
+    }
+  }
   const bool TA = (ta == 'T' || ta == 't'), TB = (tb == 'T' || tb == 't');
   constexpr int TILE = 32;
   dim3 grid((unsigned)ceil_div(N, TILE), (unsigned)ceil_div(N, TILE));

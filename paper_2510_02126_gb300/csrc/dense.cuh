@@ -4,6 +4,13 @@
 
 namespace lyap {
 
+// How gemm<double> / gemm_sym<double> compute FP64 products on the calling host thread:
+// DGEMM_AUTO (the FP16 tensor-core emulation of ozaki.cuh above a size threshold, the FP64
+// SIMT kernel below it), DGEMM_SIMT, DGEMM_TENSOR.
+enum { DGEMM_AUTO = 0, DGEMM_SIMT = 1, DGEMM_TENSOR = 2 };
+void set_dgemm_method(int method);
+int dgemm_method();
+
 // C = alpha op(A) op(B) + beta C, column-major, op = identity ('N') or transpose ('T').
 template <typename T>
 int gemm(char ta, char tb, int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t lda,

@@ -30,6 +30,9 @@ struct EigScratch {
   void (*mark)(void*, int) = nullptr;
   void* mark_ctx = nullptr;
   double* flops = nullptr;
+  // fast refinement (refine = 2) only: the relative accuracy its result must reach
+  // (remaining coupling below target ||H||_2 before it may stop); 0 = the fixed fast rule
+  double target = 0.0;
 };
 
 // H (q x q, ldh, FP64, symmetric; not modified) = Q diag(w) Q^T, w ascending,

@@ -290,165 +290,6 @@ gj_panel_kernel(int n, int k, int step, const T* __restrict__ Mcur, T* __restric
   if constexpr (CL) cluster_sync_all();  // keep shared memory alive for remote readers
 }
 
-// Single-CTA panel, thread = row (orders up to one thread per row in one CTA): thread i
-// holds the bb <= 32 panel entries of the row at position i in registers, so the
-// elimination factor of a row is its own register (no shuffle) and a column step is one
-// CTA barrier: before it every warp publishes its pivot candidate (value, row, and the
-// whole candidate row) and the thread at position g publishes row g; after it every warp
-// reduces the candidates to the pivot p (largest |a_ij| among positions >= g, lowest
-// position on ties -- the getrf choice), reads the pivot row and eliminates.  Published
-// slots are double-buffered by column parity.  Same arithmetic per element as
-// gj_panel_kernel (and the same outputs).
-template <typename T>
-struct RowPanelSh {
-  T wval[2][32];
-  int widx[2][32];
-  T wrow[2][32][GJ_BS];
-  T grow[2][GJ_BS];
-  int piv[GJ_BS];
-  int rsrc[GJ_BS];
-  float red[32];
-};
-
-__device__ __forceinline__ float block_max_f(float v, float* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  v = warp_max(v);
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  float w = (lane < nw) ? red[lane] : 0.f;
-  return warp_max(w);
-}
-
-template <typename T> struct RowPanelMax { static constexpr int threads = 1024; };
-template <> struct RowPanelMax<double> { static constexpr int threads = 512; };
-
-template <typename T, typename OP>
-__global__ void __launch_bounds__(RowPanelMax<T>::threads, 1)
-gj_panel_row_kernel(int n, int k, int step, const T* __restrict__ Mcur, T* __restrict__ Mnew,
-                    OP* __restrict__ Pp, OP* __restrict__ Rt, int* __restrict__ orig_out,
-                    const int* __restrict__ perm_old, int* __restrict__ perm_new,
-                    double* __restrict__ logpiv, int* __restrict__ ipiv, int* __restrict__ status,
-                    int* __restrict__ exps) {
-  __shared__ RowPanelSh<T> sh;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  const int bb = min(GJ_BS, n - k);
-  const int i = tid;
-  const bool live = i < n;
-  T v[GJ_BS];
-#pragma unroll
-  for (int t = 0; t < GJ_BS; ++t) v[t] = (live && t < bb) ? Mcur[(size_t)i * n + k + t] : T(0);
-
-  bool bad = false;
-#pragma unroll
-  for (int j = 0; j < GJ_BS; ++j) {
-    if (j >= bb) break;  // uniform
-    const int g = k + j, buf = j & 1;
-    T cv = T(-1);
-    int ci = -1;
-    if (live && i >= g) { cv = fabs(v[j]); ci = i; }
-    warp_argmax(cv, ci);
-    if (ci >= 0 && i == ci) {
-#pragma unroll
-      for (int t = 0; t < GJ_BS; ++t) sh.wrow[buf][warp][t] = v[t];
-    }
-    if (lane == 0) { sh.wval[buf][warp] = cv; sh.widx[buf][warp] = ci; }
-    if (i == g) {
-#pragma unroll
-      for (int t = 0; t < GJ_BS; ++t) sh.grow[buf][t] = v[t];
-    }
-    __syncthreads();
-    T pv = (lane < nw) ? sh.wval[buf][lane] : T(-1);
-    int p = (lane < nw) ? sh.widx[buf][lane] : -1;
-    warp_argmax(pv, p);
-    if (p < 0 || !(pv > T(0)) || !isfinite(pv)) {
-      if (tid == 0) atomicCAS(status, 0, (p >= 0 && (isnan(pv) || isinf(pv))) ? LYAP_ERR_NONFINITE : LYAP_ERR_SINGULAR);
-      bad = true;
-      break;  // every thread takes the same branch
-    }
-    const T* prow = sh.wrow[buf][p >> 5];
-    const T pj = prow[j];
-    const T inv = T(1) / pj;
-    if (i == g) {
-#pragma unroll
-      for (int t = 0; t < GJ_BS; ++t) v[t] = (t == j) ? inv : prow[t] * inv;
-    } else if (live) {
-      if (i == p) {
-#pragma unroll
-        for (int t = 0; t < GJ_BS; ++t) v[t] = sh.grow[buf][t];
-      }
-      const T f = v[j];
-#pragma unroll
-      for (int t = 0; t < GJ_BS; ++t) v[t] = (t == j) ? fma(-f, inv, T(0)) : fma(-f, prow[t] * inv, v[t]);
-    }
-    if (tid == 0) {
-      sh.piv[j] = p;
-      logpiv[g] = (double)pj;  // the logarithms are taken after the inversion (pivot_logs)
-      if (ipiv) ipiv[g] = p;
-    }
-  }
-  __syncthreads();
-  if (bad) return;
-
-  if (live) {
-#pragma unroll
-    for (int t = 0; t < GJ_BS; ++t)
-      if (t < bb) Mnew[(size_t)i * n + k + t] = v[t];
-    const int o = replay_swaps(i, k, bb, sh.piv);
-    orig_out[i] = o;
-    perm_new[i] = perm_old[o];
-  }
-  if (warp == 0) sh.rsrc[lane] = (lane < bb) ? replay_swaps(k + lane, k, bb, sh.piv) : 0;
-  __syncthreads();
-  constexpr int LDO = is16<OP>::value ? GJ_KLD16 : GJ_BS;
-  float sP = 1.f, sR = 1.f;
-  if constexpr (is16<OP>::value) {
-    float mp = 0.f;
-    if (live) {
-#pragma unroll
-      for (int t = 0; t < GJ_BS; ++t)
-        if (t < bb) mp = fmaxf(mp, fabsf((float)v[t] - (i == k + t ? 1.f : 0.f)));
-    }
-    float mr = 0.f;
-    if (lane < bb) {
-      const T* src = Mcur + (size_t)sh.rsrc[lane] * n;
-      for (int x = warp; x < n; x += nw)
-        if (x < k || x >= k + bb) mr = fmaxf(mr, fabsf((float)src[x]));
-    }
-    mp = block_max_f(mp, sh.red);
-    mr = block_max_f(mr, sh.red);
-    const int eP = pow2_exponent(mp), eR = pow2_exponent(mr);
-    sP = ldexpf(1.f, -eP);
-    sR = ldexpf(1.f, -eR);
-    if (tid == 0) { exps[2 * step] = eP; exps[2 * step + 1] = eR; }
-  }
-  // P' = panel - I on its diagonal block (thread = row)
-  if (live) {
-#pragma unroll
-    for (int t = 0; t < GJ_BS; ++t) {
-      const T val = (t < bb) ? v[t] - (i == k + t ? T(1) : T(0)) : T(0);
-      if constexpr (is16<OP>::value) op_store(&Pp[(size_t)i * LDO + t], (float)val * sP);
-      else op_store(&Pp[(size_t)i * LDO + t], val);
-    }
-    if constexpr (is16<OP>::value) {
-#pragma unroll
-      for (int t = GJ_BS; t < LDO; ++t) op_store(&Pp[(size_t)i * LDO + t], 0.f);
-    }
-  }
-  // R^T[x, t] = pivot row t at column x (lane = t: coalesced rows of R^T)
-  const T* srow = Mcur + (size_t)sh.rsrc[lane] * n;
-  for (int x = warp; x < n; x += nw) {
-    const bool use = lane < bb && (x < k || x >= k + bb);
-    const T val = use ? srow[x] : T(0);
-    if constexpr (is16<OP>::value) {
-      op_store(&Rt[(size_t)x * LDO + lane], (float)val * sR);
-      op_store(&Rt[(size_t)x * LDO + 32 + lane], 0.f);
-    } else {
-      op_store(&Rt[(size_t)x * LDO + lane], val);
-    }
-  }
-}
-
 // Mnew[i, x] = Mold[orig[i], x] + sum_t Pp[i, t] Rt[x, t] for x outside [k, k+bb).
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -561,25 +402,9 @@ static int panel_dispatch_g(GJWork& W, int k, int step, cudaStream_t s) {
   if (gj_panel_cluster(W.n, sizeof(T)) > 1) return launch_panel<T, NW, RPT, true, OP>(W, k, step, s);
   return launch_panel<T, NW, RPT, false, OP>(W, k, step, s);
 }
-// Largest order the single-CTA row panel takes (one thread per row; FP64 rows need twice
-// the registers).
-template <typename T> constexpr int row_panel_max_n() { return RowPanelMax<T>::threads; }
-
-template <typename T, typename OP>
-static int launch_row_panel(GJWork& W, int k, int step, cudaStream_t s) {
-  const int n = W.n;
-  const unsigned threads = (unsigned)(ceil_div(n, 32) * 32);
-  gj_panel_row_kernel<T, OP><<<1, threads, 0, s>>>(n, k, step, (const T*)W.M[W.cur], (T*)W.M[1 - W.cur], (OP*)W.Pp,
-                                                   (OP*)W.Rt, W.orig, (const int*)W.perm[W.cur], W.perm[1 - W.cur],
-                                                   W.logpiv, W.ipiv, W.status, W.exps);
-  LYAP_CUDA_TRY(cudaGetLastError());
-  lyap_count_launch();
-  return LYAP_OK;
-}
-
 template <typename T, typename OP>
 static int panel_dispatch(GJWork& W, int k, int step, cudaStream_t s) {
-  if (W.n <= row_panel_max_n<T>()) return launch_row_panel<T, OP>(W, k, step, s);
+
   const PanelGeom g = panel_geom(W.n, sizeof(T));
   if constexpr (sizeof(T) == 4) {
     if (g.rpt == 4) return panel_dispatch_g<T, 16, 4, OP>(W, k, step, s);

@@ -1,0 +1,348 @@
+// FP64 products on tcgen05 tensor cores by error-free splitting into FP16 digit slices.
+//
+// 1. Split (oz_rowexp_kernel, oz_digits_kernel): row i of op(A) gets the exponent e_i with
+//    max_l |op(A)_il| < 2^e_i; the scaled row a = op(A)_i. 2^-e_i in (-1, 1) is cut into
+//    OZ_SLICES digits, d_s = rint(2^OZ_BETA r_{s-1}), r_s = 2^OZ_BETA r_{s-1} - d_s (every
+//    step exact in FP64), stored as FP16 integers in K-major slices (slice s at rows
+//    [s Mp, (s+1) Mp) of one tall array).  op(B) is split the same way by columns.
+// 2. Product (oz_gemm_kernel): one CTA per 128 x 64 tile of C.  A producer warp streams the
+//    digit tiles by TMA through a ring of shared-memory stages and issues tcgen05.mma
+//    (kind::f16, FP32 accumulators in TMEM) for every pair (s, t) with s + t <= OZ_SLICES + 1
+//    over K chunks of OZ_KCHUNK; each pair's integer product is exact in FP32.  Two TMEM
+//    accumulators alternate: while the MMAs of one pair fill one, four epilogue warps drain
+//    the other into FP64 registers (scaled by 2^(-OZ_BETA (s + t)), deepest pairs first).
+//    The tile is finally scaled by 2^(e_i + f_j), alpha and beta applied, and stored.
+// Every mbarrier wait is bounded: on timeout the CTA records LYAP_ERR_TIMEOUT, lets its copies
+// land, frees its TMEM and returns.
+#include "ozaki.cuh"
+#include "tc_gemm.cuh"
+#include "tc_ptx.cuh"
+
+namespace lyap {
+
+constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 64, OZ_STAGES = 4;
+constexpr int OZ_A_BYTES = OZ_BM * OZ_BK * 2;  // 16 KB
+constexpr int OZ_B_BYTES = OZ_BN * OZ_BK * 2;  // 8 KB
+constexpr int OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;
+constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE_BYTES + 1024 + 256;
+constexpr int OZ_NPAIRS = OZ_SLICES * (OZ_SLICES + 1) / 2;  // pairs with s + t <= S + 1 (s, t >= 1)
+constexpr int OZ_THREADS = 160;                             // 4 epilogue warps + 1 producer warp
+
+// ---------------------------------------------------------------------------
+// split
+// ---------------------------------------------------------------------------
+// e[r] = exponent with max_l |x(r, l)| < 2^e[r] (0 for a zero row); x(r, l) = X[r + l ld]
+// (tr = 0) or X[l + r ld] (tr = 1)
+__global__ void oz_rowexp_kernel(const double* __restrict__ X, int64_t ld, int tr, int64_t R, int64_t K,
+                                 int* __restrict__ e) {
+  if (tr == 0) {
+    // thread per row: consecutive rows are contiguous, so every step of l is coalesced
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    double m = 0.0;
+    for (int64_t l = 0; l < K; ++l) m = fmax(m, fabs(X[r + l * ld]));
+    int ex = 0;
+    if (m > 0.0) frexp(m, &ex);
+    e[r] = ex;
+  } else {
+    // warp per row: the row is contiguous
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= R) return;
+    double m = 0.0;
+    for (int64_t l = lane; l < K; l += 32) m = fmax(m, fabs(X[l + r * ld]));
+    m = warp_max(m);
+    if (lane == 0) {
+      int ex = 0;
+      if (m > 0.0) frexp(m, &ex);
+      e[r] = ex;
+    }
+  }
+}
+
+// digits of the 32 x 32 tile (rows r0.., columns l0..) into the slices (zeros in the padding)
+__global__ void __launch_bounds__(256) oz_digits_kernel(const double* __restrict__ X, int64_t ld, int tr, int64_t R,
+                                                        int64_t K, const int* __restrict__ e, __half* __restrict__ D,
+                                                        int64_t Rp, int64_t Kp) {
+  __shared__ double t[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, l0 = (int64_t)blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int k = ty; k < 32; k += 8) {
+    // tr = 0: consecutive tx -> consecutive rows (contiguous); tr = 1: consecutive columns
+    if (tr == 0) {
+      const int64_t r = r0 + tx, l = l0 + k;
+      t[tx][k] = (r < R && l < K) ? X[r + l * ld] : 0.0;
+    } else {
+      const int64_t r = r0 + k, l = l0 + tx;
+      t[k][tx] = (r < R && l < K) ? X[l + r * ld] : 0.0;
+    }
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    const int64_t r = r0 + k, l = l0 + tx;
+    if (r >= Rp || l >= Kp) continue;
+    double a = (r < R) ? ldexp(t[k][tx], -e[r]) : 0.0;
+#pragma unroll
+    for (int s = 0; s < OZ_SLICES; ++s) {
+      const double u = a * (double)(1 << OZ_BETA);
+      const double d = rint(u);
+      a = u - d;
+      D[(size_t)s * Rp * Kp + (size_t)r * Kp + l] = __float2half_rn((float)d);  // |d| <= 2^OZ_BETA: exact
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// product
+// ---------------------------------------------------------------------------
+struct OzPairs {
+  unsigned char s[OZ_NPAIRS], t[OZ_NPAIRS];
+};
+// (s, t), 0-based, ordered by descending level s + t (the smallest terms are summed first)
+static constexpr OzPairs oz_make_pairs() {
+  OzPairs p{};
+  int k = 0;
+  for (int lev = OZ_SLICES - 1; lev >= 0; --lev)
+    for (int s = 0; s <= lev; ++s) {
+      p.s[k] = (unsigned char)s;
+      p.t[k] = (unsigned char)(lev - s);
+      ++k;
+    }
+  return p;
+}
+__constant__ OzPairs c_oz_pairs = oz_make_pairs();
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
+               int64_t Mp, int64_t Np, int nkb, const int* __restrict__ eA, const int* __restrict__ eB, double alpha,
+               double beta, double* __restrict__ C, int64_t ldc, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + OZ_STAGES * OZ_STAGE_BYTES);
+  uint64_t* empty = full + OZ_STAGES;
+  uint64_t* accfull = empty + OZ_STAGES;  // [2]
+  uint64_t* accempty = accfull + 2;       // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accempty + 2);
+  __shared__ int fail_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * OZ_BM, n0 = blockIdx.x * OZ_BN;
+  const int nchunk = (nkb + OZ_KCHUNK / OZ_BK - 1) / (OZ_KCHUNK / OZ_BK);
+  const int total = nchunk * OZ_NPAIRS;  // accumulations (pairs x chunks)
+
+  if (tid == 0) {
+    for (int s = 0; s < OZ_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accfull[b], 1);
+      mbar_init(&accempty[b], 4);
+    }
+    fail_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, 2 * OZ_BN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 4) {
+    // ---------------- producer: TMA loads and MMA issue (one thread) ----------------
+    // Iteration `it` is one k-block of one accumulation (chunk, pair); chunks are full
+    // (OZ_KCHUNK / OZ_BK k-blocks) but the last.  Loads run OZ_STAGES iterations ahead.
+    if (lane == 0) {
+      constexpr int KBC = OZ_KCHUNK / OZ_BK;
+      const int per_chunk = KBC * OZ_NPAIRS;
+      const int last_len = nkb - (nchunk - 1) * KBC;
+      const int total_it = (nchunk - 1) * per_chunk + last_len * OZ_NPAIRS;
+      auto decode = [&](int x, int& pi, int& kb, int& first, int& last) {
+        const int c = min(x / per_chunk, nchunk - 1);
+        const int off = x - c * per_chunk;
+        const int len = (c == nchunk - 1) ? last_len : KBC;
+        pi = off / len;
+        const int kk = off - pi * len;
+        kb = c * KBC + kk;
+        first = (kk == 0);
+        last = (kk == len - 1);
+      };
+      auto issue = [&](int x) {
+        int pi, kb, f, l;
+        decode(x, pi, kb, f, l);
+        const int st = x % OZ_STAGES;
+        unsigned char* sa = base + st * OZ_STAGE_BYTES;
+        mbar_expect_tx(&full[st], OZ_STAGE_BYTES);
+        tma_load_2d(sa, &tmA, kb * OZ_BK, (int)(c_oz_pairs.s[pi] * Mp + m0), &full[st]);
+        tma_load_2d(sa + OZ_A_BYTES, &tmB, kb * OZ_BK, (int)(c_oz_pairs.t[pi] * Np + n0), &full[st]);
+      };
+      const uint32_t idesc = make_idesc_mn(0, OZ_BM, OZ_BN);
+      int issued = 0;
+      for (; issued < total_it && issued < OZ_STAGES; ++issued) issue(issued);
+      bool ok = true;
+      int a = -1;  // current accumulation
+      for (int it = 0; it < total_it; ++it) {
+        int pi, kb, first, last;
+        decode(it, pi, kb, first, last);
+        const int st = it % OZ_STAGES;
+        const unsigned ph = (unsigned)(it / OZ_STAGES) & 1u;
+        if (first) {
+          ++a;
+          const int use = a >> 1;
+          if (use > 0 && !mbar_wait(&accempty[a & 1], (unsigned)(use - 1) & 1u)) { ok = false; break; }
+        }
+        if (!mbar_wait(&full[st], ph)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t dcol = tmem + (uint32_t)((a & 1) * OZ_BN);
+        unsigned char* sa = base + st * OZ_STAGE_BYTES;
+        const uint64_t ad = smem_desc_sw128(sa);
+        const uint64_t bd = smem_desc_sw128(sa + OZ_A_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < OZ_BK / 16; ++kk) tc_mma(dcol, ad + 2 * kk, bd + 2 * kk, idesc, (!first || kk > 0) ? 1 : 0);
+        tc_commit(&empty[st]);
+        if (last) tc_commit(&accfull[a & 1]);
+        // refill this stage with the load OZ_STAGES iterations ahead once its MMAs are done
+        if (issued < total_it) {
+          if (!mbar_wait(&empty[st], ph)) { ok = false; break; }
+          issue(issued);
+          ++issued;
+        }
+      }
+      if (!ok) {
+        atomicCAS(status, 0, LYAP_ERR_TIMEOUT);
+        fail_s = 1;
+        // let the copies in flight land before the CTA exits (bounded waits)
+        for (int x = max(0, issued - OZ_STAGES); x < issued; ++x)
+          (void)mbar_wait(&full[x % OZ_STAGES], (unsigned)(x / OZ_STAGES) & 1u);
+      }
+    }
+  } else {
+    // ---------------- epilogue warps 0..3: TMEM lanes 32 w .. 32 w + 31 ----------------
+    double acc[OZ_BN];
+#pragma unroll
+    for (int j = 0; j < OZ_BN; ++j) acc[j] = 0.0;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    bool ok = true;
+    for (int a = 0; a < total; ++a) {
+      const int pi = a % OZ_NPAIRS;
+      const int b = a & 1, use = a >> 1;
+      if (!mbar_wait(&accfull[b], (unsigned)use & 1u)) { ok = false; break; }
+      tc_fence_after();
+      const double sc = ldexp(1.0, -OZ_BETA * (c_oz_pairs.s[pi] + c_oz_pairs.t[pi] + 2));
+#pragma unroll
+      for (int j0 = 0; j0 < OZ_BN; j0 += 16) {
+        float v[16];
+        tmem_ld16(lane_base + (uint32_t)(b * OZ_BN + j0), v);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) acc[j0 + u] = fma(sc, (double)v[u], acc[j0 + u]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&accempty[b]);
+    }
+    if (!ok) atomicCAS(status, 0, LYAP_ERR_TIMEOUT);
+    const int row = m0 + warp * 32 + lane;
+    if (ok && row < M) {
+      const int ea = eA[row];
+#pragma unroll
+      for (int j = 0; j < OZ_BN; ++j) {
+        const int col = n0 + j;
+        if (col < N) {
+          double* c = C + (size_t)row + (size_t)col * ldc;
+          const double v = alpha * ldexp(acc[j], ea + eB[col]);
+          *c = (beta == 0.0) ? v : fma(beta, *c, v);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 2 * OZ_BN);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+struct OzBufs {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+thread_local OzBufs g_oz;
+
+int oz_ensure(size_t bytes) {
+  if (g_oz.p && g_oz.cap >= bytes) return LYAP_OK;
+  if (g_oz.p) {
+    // work queued on any stream may still read the old buffer
+    LYAP_CUDA_TRY(cudaDeviceSynchronize());
+    cudaFree(g_oz.p);
+    g_oz.p = nullptr;
+    g_oz.cap = 0;
+  }
+  const size_t want = bytes + bytes / 4 + 4096;
+  if (cudaMalloc(&g_oz.p, want) != cudaSuccess) {
+    cudaGetLastError();
+    lyap_set_error_message("device allocation failed (FP64 tensor-core products)", __FILE__, __LINE__);
+    return LYAP_ERR_NOMEM;
+  }
+  g_oz.cap = want;
+  return LYAP_OK;
+}
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+int oz_split(const double* X, int64_t ld, int tr, int64_t R, int64_t K, int64_t Rp, int64_t Kp, int* e, __half* D,
+             cudaStream_t s) {
+  if (tr == 0) oz_rowexp_kernel<<<(unsigned)ceil_div(R, 128), 128, 0, s>>>(X, ld, 0, R, K, e);
+  else oz_rowexp_kernel<<<(unsigned)ceil_div(R * 32, 256), 256, 0, s>>>(X, ld, 1, R, K, e);
+  dim3 g((unsigned)(Kp / 32), (unsigned)(Rp / 32));
+  oz_digits_kernel<<<g, 256, 0, s>>>(X, ld, tr, R, K, e, D, Rp, Kp);
+  LYAP_CUDA_TRY(cudaGetLastError());
+  lyap_count_launch(2);
+  return LYAP_OK;
+}
+}  // namespace
+
+int ozaki_dgemm(char ta, char tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
+                const double* B, int64_t ldb, double beta, double* C, int64_t ldc, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return LYAP_OK;
+  if (K <= 0 || alpha == 0.0) {
+    if (beta == 0.0) return set_zero<double>(C, M, N, ldc, s);
+    return gemm<double>('N', 'N', M, N, 0, 0.0, A, lda, B, ldb, beta, C, ldc, s);
+  }
+  const int64_t Mp = round_up(M, OZ_BM), Np = round_up(N, OZ_BN), Kp = round_up(K, OZ_BK);
+  if (Mp * OZ_SLICES > INT32_MAX || Np * OZ_SLICES > INT32_MAX || Kp > INT32_MAX) return LYAP_ERR_ARG;
+  // workspace: digit slices of op(A) (S Mp x Kp) and of op(B)^T (S Np x Kp), exponents
+  const size_t bA = (size_t)OZ_SLICES * Mp * Kp * 2, bB = (size_t)OZ_SLICES * Np * Kp * 2;
+  const size_t bE = (size_t)(Mp + Np) * 4;
+  LYAP_TRY(oz_ensure(bA + bB + bE + 512));
+  __half* DA = static_cast<__half*>(g_oz.p);
+  __half* DB = reinterpret_cast<__half*>(static_cast<char*>(g_oz.p) + bA);
+  int* eA = reinterpret_cast<int*>(static_cast<char*>(g_oz.p) + bA + bB);
+  int* eB = eA + Mp;
+  // op(A) rows: A[i + l lda] ('N') or A[l + i lda] ('T');
+  // op(B)^T rows (= columns of op(B)): B[l + j ldb] ('N') or B[j + l ldb] ('T')
+  LYAP_TRY(oz_split(A, lda, (ta == 'T' || ta == 't') ? 1 : 0, M, K, Mp, Kp, eA, DA, s));
+  LYAP_TRY(oz_split(B, ldb, (tb == 'T' || tb == 't') ? 0 : 1, N, K, Np, Kp, eB, DB, s));
+  CUtensorMap mA, mB;
+  LYAP_TRY(tc_make_map(&mA, DA, LYAP_FP16, (int64_t)OZ_SLICES * Mp, Kp, Kp, OZ_BM));
+  LYAP_TRY(tc_make_map(&mB, DB, LYAP_FP16, (int64_t)OZ_SLICES * Np, Kp, Kp, OZ_BN));
+  static DeviceOnce attr;
+  if (attr.need()) {
+    LYAP_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+    attr.set();
+  }
+  int* st = tc_status_word();
+  if (!st) return LYAP_ERR_NOMEM;
+  dim3 grid((unsigned)(Np / OZ_BN), (unsigned)(Mp / OZ_BM));
+  oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM, s>>>(mA, mB, (int)M, (int)N, Mp, Np, (int)(Kp / OZ_BK), eA, eB, alpha,
+                                                   beta, C, ldc, st);
+  LYAP_CUDA_TRY(cudaGetLastError());
+  lyap_count_launch();
+  return LYAP_OK;
+}
+
+}  // namespace lyap

@@ -1423,7 +1423,7 @@ static int res_fac(Ctx& C, const Problem& pb, const double* Lw, const double* sd
 // G = [Z, Z+, Z-] (Cholesky) or [Z, Z^Delta] with weights ups (LDL^T), in C.G.
 // ---------------------------------------------------------------------------
 static int sol_upt(Ctx& C, int n, int qg, int cneg_start, const double* ups, bool psd_keep_positive,
-                   double eta_s, double* Zout, double* yout, int* r_out) {
+                   double eta_s, double res_next, double* Zout, double* yout, int* r_out) {
   double* G = P<double>(C.G);
   mark(C, LYAP_PHASE_SOLUPT);
   LYAP_TRY(ensure(C.tau, (size_t)(qg + 8) * 8));
@@ -1444,7 +1444,13 @@ static int sol_upt(Ctx& C, int n, int qg, int cneg_start, const double* ups, boo
                         C.s));
   LYAP_TRY(prepare_eig(C, kr));
   mark(C, LYAP_PHASE_EIG);
-  LYAP_TRY(sym_eig(P<double>(C.H), kr, kr, P<double>(C.w), P<double>(C.Qh), kr, 2, C.eig, C.s));
+  // the eigendecomposition of K defines X_{i+1}: its error enters the next residual, so the
+  // fast refinement runs until its coupling is below 1/100 of the residual this step is
+  // expected to reach (res_next), and at most to FP64 level
+  C.eig.target = std::max(1e-15, 1e-2 * res_next);
+  const int est = sym_eig(P<double>(C.H), kr, kr, P<double>(C.w), P<double>(C.Qh), kr, 2, C.eig, C.s);
+  C.eig.target = 0.0;
+  LYAP_TRY(est);
   mark(C, LYAP_PHASE_SOLUPT);
   int* sel = P<int>(C.scal) + 64;
   select_kernel<<<1, 32, 0, C.s>>>(P<double>(C.w), kr, eta_s, 0, sel, P<double>(C.scal) + 31);
@@ -1571,6 +1577,11 @@ static int solve_common(Ctx& C, const Problem& pb, const lyap_opts_t& o, bool re
     if (!refine) break;
     if (res_prev > 0 && ro.res / res_prev > o.stag_theta) ++stag;
     else stag = 0;
+    // the residual this step is expected to reach: the last observed contraction (first step:
+    // a guess from u_s -- roughly the contraction of the inner solves at moderate kappa)
+    double contraction = (o.u_s == LYAP_FP64) ? 1e-8 : (o.u_s == LYAP_FP32) ? 1e-5 : (o.u_s == LYAP_FP16) ? 1e-2 : 1e-1;
+    if (res_prev > 0) contraction = std::min(1.0, std::max(1e-8, ro.res / res_prev));
+    const double res_next = ro.res * contraction;
     res_prev = ro.res;
     if (stag >= o.stag_count) {
       info->stagnated = 1;
@@ -1601,7 +1612,7 @@ static int solve_common(Ctx& C, const Problem& pb, const lyap_opts_t& o, bool re
       info->newton_calls += 1;
       info->newton_total += C.store_count;
       int rnew = 0;
-      LYAP_TRY(sol_upt(C, n, c + cp + cm, c + cp, nullptr, true, eta_s, P<double>(C.Zs), nullptr, &rnew));
+      LYAP_TRY(sol_upt(C, n, c + cp + cm, c + cp, nullptr, true, eta_s, res_next, P<double>(C.Zs), nullptr, &rnew));
       c = rnew;
     } else {
       LYAP_TRY(ensure(C.Vs, (size_t)n * (rp + 1) * 8 + 64));
@@ -1619,7 +1630,7 @@ static int solve_common(Ctx& C, const Problem& pb, const lyap_opts_t& o, bool re
       info->newton_calls += 1;
       info->newton_total += C.store_count;
       int rnew = 0;
-      LYAP_TRY(sol_upt(C, n, c + cp, c + cp, ups, project, eta_s, P<double>(C.Zs), P<double>(C.ysol), &rnew));
+      LYAP_TRY(sol_upt(C, n, c + cp, c + cp, ups, project, eta_s, res_next, P<double>(C.Zs), P<double>(C.ysol), &rnew));
       c = rnew;
     }
     info->ir_steps = i;
@@ -1657,9 +1668,16 @@ static int solve_entry(lyap_ctx_t* C, const double* A, int64_t n, int64_t lda, c
   C->marks_used = 0;
   C->recomputed = 0;
   for (double& f : C->flops) f = 0.0;
+  const int dgemm_prev = dgemm_method();
+  set_dgemm_method(opts->fp64_products);
   cudaEventRecord(C->e0, C->s);
   mark(*C, LYAP_PHASE_OTHER);
   int st = solve_common(*C, pb, *opts, refine, Z, ldz, z_cap, D, rank_out, inf);
+  set_dgemm_method(dgemm_prev);
+  if (st >= 0) {
+    int tcs = 0;  // a bounded wait of a tensor-core product that gave up
+    if (tc_status_read(&tcs) == LYAP_OK && tcs) st = tcs;
+  }
   collect_marks(*C, inf);
   C->profile = false;
   cudaEventRecord(C->e1, C->s);
@@ -1696,6 +1714,8 @@ static int adjoint_entry(lyap_ctx_t* Cp, const double* A, int64_t n, int64_t lda
   C.marks_used = 0;
   C.recomputed = 0;
   for (double& f : C.flops) f = 0.0;
+  const int dgemm_prev = dgemm_method();
+  set_dgemm_method(opts->fp64_products);
   cudaEventRecord(C.e0, C.s);
   mark(C, LYAP_PHASE_OTHER);
   int st = LYAP_OK;
@@ -1796,6 +1816,7 @@ static int adjoint_entry(lyap_ctx_t* Cp, const double* A, int64_t n, int64_t lda
     const int t = transpose_store(C);
     if (st >= 0 && t < 0) st = t;
   }
+  set_dgemm_method(dgemm_prev);
   collect_marks(C, inf);
   C.profile = false;
   cudaEventRecord(C.e1, C.s);
@@ -1938,6 +1959,25 @@ int lyap_residual(lyap_ctx_t* C, const double* A, int64_t n, int64_t lda, const 
                    &ro));
   *res_out = ro.res;
   return LYAP_OK;
+}
+
+int lyap_dgemm(lyap_ctx_t* C, char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+               const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* Cm, int64_t ldc,
+               int method) {
+  const bool ta = (transa == 'T' || transa == 't'), tb = (transb == 'T' || transb == 't');
+  if (!C || m < 0 || n < 0 || k < 0 || method < 0 || method > 2) return LYAP_ERR_ARG;
+  if ((transa != 'N' && transa != 'n' && !ta) || (transb != 'N' && transb != 'n' && !tb)) return LYAP_ERR_ARG;
+  if (m == 0 || n == 0) return LYAP_OK;
+  if (!Cm || ldc < m || (k > 0 && (!A || !B || lda < (ta ? k : m) || ldb < (tb ? n : k)))) return LYAP_ERR_ARG;
+  const int prev = dgemm_method();
+  set_dgemm_method(method);
+  int st = gemm<double>(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc, C->s);
+  set_dgemm_method(prev);
+  LYAP_TRY(st);
+  LYAP_CUDA_TRY(cudaStreamSynchronize(C->s));
+  int tcs = 0;
+  LYAP_TRY(tc_status_read(&tcs));
+  return tcs;
 }
 
 int lyap_trace_loss(lyap_ctx_t* C, const double* Z, int64_t n, int64_t ldz, int64_t r, const double* D,

@@ -14,6 +14,7 @@
 
 #include "gj_inverse.cuh"
 #include "tc_gemm.cuh"
+#include "tc_ptx.cuh"
 
 #include <atomic>
 
@@ -29,91 +30,8 @@ __host__ __device__ constexpr int tc_smem(int mode) { return tc_stages(mode) * 2
 // epilogue staging of the update (per warp 32 x 33 floats) fits in the stage buffers
 static_assert(4 * 32 * 33 * 4 <= 2 * TC_TILE_BYTES, "staging area");
 
-// ---------------------------------------------------------------------------
-// PTX wrappers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n"
-      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait: false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  for (unsigned it = 0; it < (1u << 22); ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, unsigned ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
-               "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, unsigned ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n"
-      " setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-      : "memory");
-}
-__device__ __forceinline__ void tc_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// K-major operand tile of 128 rows x 64 16-bit elements, 128-byte swizzle:
-// 8-row swizzle atoms of 1024 bytes stacked along M/N (stride byte offset 1024).
-__device__ __forceinline__ uint64_t smem_desc_sw128(const void* p) {
-  const uint64_t addr = smem_u32(p);
-  uint64_t d = 0;
-  d |= (addr >> 4) & 0x3FFFull;                 // start address
-  d |= (uint64_t)(16 >> 4) << 16;               // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;             // stride byte offset
-  d |= 1ull << 46;                              // descriptor version (sm_100 family)
-  d |= 2ull << 61;                              // SWIZZLE_128B
-  return d;
-}
-// instruction descriptor: D = F32, A/B = F16 (fmt 0) or BF16 (fmt 1), both K-major, M = 128, N = TC_BN
-__host__ __device__ constexpr uint32_t make_idesc(int fmt) {
-  return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
-         ((uint32_t)(TC_BM >> 4) << 24);
-}
+// instruction descriptor for the 128 x 128 tiles of this file
+__host__ __device__ constexpr uint32_t make_idesc(int fmt) { return make_idesc_mn(fmt, TC_BM, TC_BN); }
 
 struct EpiGJ {
   const float* Mcur;
@@ -229,12 +147,17 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         __syncwarp();
         const int x = n0 + j0 + lane;
         const bool xok = x < eg.n && (x < eg.k || x >= eg.k + eg.bb);
-#pragma unroll 4
+        // all 32 row loads of the block are issued before any is used (memory-level
+        // parallelism: the old rows come from DRAM at large n)
+        float old[32];
+#pragma unroll
         for (int rr = 0; rr < 32; ++rr) {
           const int src = __shfl_sync(0xffffffffu, my_src, rr);
-          if (rbase + rr < eg.n && xok)
-            eg.Mnew[(size_t)(rbase + rr) * eg.n + x] = eg.Mcur[(size_t)src * eg.n + x] + sc * stg[rr * 33 + lane];
+          old[rr] = (rbase + rr < eg.n && xok) ? __ldcs(eg.Mcur + (size_t)src * eg.n + x) : 0.f;
         }
+#pragma unroll
+        for (int rr = 0; rr < 32; ++rr)
+          if (rbase + rr < eg.n && xok) __stcs(eg.Mnew + (size_t)(rbase + rr) * eg.n + x, old[rr] + sc * stg[rr * 33 + lane]);
       }
     } else {
       const int ex = *ep.eX;
@@ -273,8 +196,8 @@ static EncodeTiledFn get_encode() {
   return fn;
 }
 
-// 2-D map over a row-major [rows x cols] 16-bit array with row pitch ld (elements); box 64 x 128
-static int make_map(CUtensorMap* map, const void* ptr, int prec, int64_t rows, int64_t cols, int64_t ld) {
+// 2-D map over a row-major [rows x cols] 16-bit array with row pitch ld (elements); box 64 x box_rows
+int tc_make_map(CUtensorMap* map, const void* ptr, int prec, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
   EncodeTiledFn enc = get_encode();
   if (!enc) {
     lyap_set_error_message("cuTensorMapEncodeTiled unavailable", __FILE__, __LINE__);
@@ -283,7 +206,7 @@ static int make_map(CUtensorMap* map, const void* ptr, int prec, int64_t rows, i
   const CUtensorMapDataType dt = (prec == LYAP_BF16) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t gstride[1] = {(cuuint64_t)(ld * 2)};
-  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)TC_BM};
+  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, dt, 2, const_cast<void*>(ptr), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -311,7 +234,7 @@ static int cached_map(MapCache* cache, int ncache, const void* ptr, int prec, in
   }
   static thread_local int victim = 0;
   MapCache& c = cache[victim++ % ncache];
-  LYAP_TRY(make_map(&c.map, ptr, prec, rows, cols, ld));
+  LYAP_TRY(tc_make_map(&c.map, ptr, prec, rows, cols, ld, TC_BM));
   c.ptr = ptr;
   c.prec = prec;
   c.rows = rows;
@@ -325,7 +248,7 @@ static int cached_map(MapCache* cache, int ncache, const void* ptr, int prec, in
 static thread_local MapCache g_cache[16];
 
 static thread_local int* g_status = nullptr;
-static int* status_word() {
+int* tc_status_word() {
   int*& p = g_status;
   if (!p) {
     if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
@@ -343,7 +266,7 @@ static int launch_tc(int mode, int prec, const CUtensorMap& a, const CUtensorMap
     LYAP_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(1)));
     attr.set();
   }
-  int* st = status_word();
+  int* st = tc_status_word();
   if (!st) return LYAP_ERR_NOMEM;
   dim3 grid((unsigned)ceil_div(N, TC_BN), (unsigned)ceil_div(M, TC_BM));
   const int fmt = (prec == LYAP_BF16) ? 1 : 0;
@@ -364,9 +287,10 @@ void tc_release_thread_state() {
 }
 
 int tc_status_read(int* out) {
-  int* st = status_word();
+  int* st = tc_status_word();
   if (!st) return LYAP_ERR_NOMEM;
   LYAP_CUDA_TRY(cudaMemcpy(out, st, sizeof(int), cudaMemcpyDeviceToHost));  // after the caller's stream sync
+  if (*out) LYAP_CUDA_TRY(cudaMemset(st, 0, sizeof(int)));                     // reported once
   return LYAP_OK;
 }
 

@@ -1,5 +1,7 @@
 // tcgen05 tensor-core GEMMs (sm_103a): TMA-fed 16-bit operands, FP32 accumulators in TMEM.
 #pragma once
+#include <cuda.h>
+
 #include "lyap_common.cuh"
 
 namespace lyap {
@@ -33,5 +35,12 @@ int tc_status_read(int* out);
 void tc_release_thread_state();
 
 int factor_to_16(int prec, const float* Z, int n, int c, int64_t ld, void* Zh, int* eZ, cudaStream_t s);
+
+// The calling host thread's device status word of the tensor-core kernels (nullptr if it
+// cannot be allocated); kernels record LYAP_ERR_TIMEOUT there.
+int* tc_status_word();
+// Encode a TMA map over a row-major [rows x cols] 16-bit array of precision prec with row
+// pitch ld (elements), box 64 (K) x box_rows, 128-byte swizzle.
+int tc_make_map(CUtensorMap* map, const void* ptr, int prec, int64_t rows, int64_t cols, int64_t ld, int box_rows);
 
 }  // namespace lyap

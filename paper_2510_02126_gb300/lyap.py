@@ -35,7 +35,8 @@ class LyapOpts(C.Structure):
         ("stop_after", C.c_int), ("delta_rule", C.c_int), ("scale_off", C.c_double), ("rank_tol", C.c_double),
         ("rho", C.c_double), ("kmax", C.c_int), ("imax", C.c_int), ("tau_ir", C.c_double), ("eta_r", C.c_double),
         ("eta_s", C.c_double), ("stag_theta", C.c_double), ("stag_count", C.c_int), ("project_psd", C.c_int),
-        ("profile", C.c_int), ("ckpt_every", C.c_int), ("mem_budget", C.c_int64), ("reserved", C.c_int * 4),
+        ("profile", C.c_int), ("ckpt_every", C.c_int), ("mem_budget", C.c_int64), ("fp64_products", C.c_int),
+        ("reserved", C.c_int * 3),
     ]
 
 
@@ -90,6 +91,7 @@ SIGNATURES = {
     "lyap_adjoint": (C.c_int, [_P, _P, _I64, _I64, _P, _I64, _I64, _P, _I64, _P, _I64, _I64, _P, _P, _I64, _I64,
                                C.POINTER(LyapOpts), _P, _I64, _P, _I64, _P, _I64, _P, _I64, _I64, C.POINTER(_I64),
                                C.POINTER(LyapInfo)]),
+    "lyap_dgemm": (C.c_int, [_P, C.c_char, C.c_char, _I64, _I64, _I64, _D, _P, _I64, _P, _I64, _D, _P, _I64, C.c_int]),
     "lyap_trace_loss": (C.c_int, [_P, _P, _I64, _I64, _I64, _P, _P, _I64, _I64, C.POINTER(_D), _P, _I64]),
     "lyap_rank_trunc": (C.c_int, [_P, _P, _I64, _I64, _I64, _D, C.POINTER(_I64)]),
     "lyap_sym_eig": (C.c_int, [_P, _P, _I64, _I64, _P, _P, _I64, C.c_int]),
@@ -353,6 +355,27 @@ def residual(A, L, Z, S=None, D=None) -> float:
     return out.value
 
 
+DGEMM = {"auto": 0, "simt": 1, "tensor": 2}
+
+
+def dgemm(A, B, ta="N", tb="N", alpha=1.0, beta=0.0, C=None, method="auto"):
+    """C = alpha op(A) op(B) + beta C in FP64 (lyap_dgemm): method "simt", "tensor" (FP64
+    emulated on the FP16 tensor cores) or "auto"."""
+    ctx = context()
+    A, B = _cm(A), _cm(B)
+    m = A.shape[1] if ta == "T" else A.shape[0]
+    k = A.shape[0] if ta == "T" else A.shape[1]
+    n = B.shape[0] if tb == "T" else B.shape[1]
+    if C is None:
+        C = cm_empty(m, n, A.device)
+    else:
+        C = _cm(C)
+    _check(ctx.lib.lyap_dgemm(ctx.h, ta.encode(), tb.encode(), m, n, k, float(alpha), _P(A.data_ptr()), A.shape[0],
+                              _P(B.data_ptr()), B.shape[0], float(beta), _P(C.data_ptr()), C.shape[0],
+                              DGEMM[method] if isinstance(method, str) else int(method)), allow_warn=False)
+    return C
+
+
 def invert(A, prec="fp64"):
     """Blocked Gauss-Jordan inverse with partial pivoting: returns (Ainv, ipiv, logabsdet)."""
     ctx = context()
@@ -422,4 +445,5 @@ lyap_adjoint = adjoint
 lyap_solve_ir_batched = solve_ir_batched
 lyap_rank_trunc = rank_trunc
 lyap_trace_loss = trace_loss_value
+lyap_dgemm = dgemm
 lyap_sym_eig = sym_eig

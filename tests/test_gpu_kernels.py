@@ -159,3 +159,49 @@ def test_sym_eig_order_beyond_split_grid(refine):
     assert np.max(np.abs(Q.T @ Q - np.eye(q))) <= (1e-13 if refine else 1e-4)
     S = Q.T @ H @ Q
     assert np.linalg.norm(S - np.diag(np.diag(S)), 2) <= tol * nh * (1 if refine else q ** 0.5)
+
+
+# ------------------------------------------------ FP64 products on the tensor cores
+
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (5, 7, 3), (128, 64, 64), (300, 200, 1100), (1000, 421, 1024),
+                                   (130, 129, 2050)])
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
+def test_dgemm_tensor_emulation_fp64_accuracy(m, n, k, ta, tb):
+    # lyap_dgemm method 2 (FP16 digit slices on tcgen05, FP64 sums) against the exact product's
+    # FP64 error bound: |C - AB|_ij <= 4 k u max_l|a_il| max_l|b_lj| + 64 u (|A||B|)_ij
+    g = gen.rng(3000 + m + 7 * n + 13 * k)
+    A = g.standard_normal((k, m) if ta == "T" else (m, k))
+    B = g.standard_normal((n, k) if tb == "T" else (k, n))
+    A *= 2.0 ** g.integers(-20, 20, size=(A.shape[0], 1))  # graded rows
+    C0 = g.standard_normal((m, n))
+    opA = A.T if ta == "T" else A
+    opB = B.T if tb == "T" else B
+    for alpha, beta in ((1.0, 0.0), (-0.5, 2.0)):
+        C = lib().dgemm(T(A), T(B), ta, tb, alpha=alpha, beta=beta, C=T(C0), method="tensor")
+        ref = alpha * (opA @ opB) + beta * C0
+        u = 2.0 ** -53
+        bound = (4 * k * u * np.abs(alpha) * np.max(np.abs(opA), axis=1)[:, None] * np.max(np.abs(opB), axis=0)[None, :]
+                 + 64 * u * (np.abs(alpha) * np.abs(opA) @ np.abs(opB) + np.abs(beta * C0)))
+        err = np.abs(N(C) - ref)
+        assert np.all(err <= bound), (float(np.max(err / bound)))
+
+
+def test_dgemm_tensor_matches_simt_and_exact_integers():
+    # integer matrices whose products are exact in FP64: every method returns them exactly
+    g = gen.rng(3100)
+    A = g.integers(-1000, 1000, size=(257, 333)).astype(np.float64)
+    B = g.integers(-1000, 1000, size=(333, 190)).astype(np.float64)
+    ref = A @ B
+    for method in ("tensor", "simt", "auto"):
+        C = N(lib().dgemm(T(A), T(B), method=method))
+        assert np.array_equal(C, ref), method
+
+
+def test_dgemm_zero_and_empty():
+    A = np.zeros((64, 40))
+    B = np.ones((40, 30))
+    C = N(lib().dgemm(T(A), T(B), method="tensor"))
+    assert np.all(C == 0.0)
+    C0 = np.full((64, 30), 3.0)
+    C = N(lib().dgemm(T(np.zeros((64, 0))), T(np.zeros((0, 30))), beta=1.0, C=T(C0), method="tensor"))
+    assert np.array_equal(C, C0)
