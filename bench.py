@@ -419,6 +419,7 @@ def run_case(args):
                         H = T P T^T (T upper triangular, P = diag(+-1)), the shape of the
                         residual cores of the refinement
     solve:<u_s>         one lyap_solve_ir of the benchmark workload
+    lowrank:<n>:<q>:<u> one solve of the Sec. 4.2 family (IR at u, or the FP64 sign-Newton for fp64)
     table41[:n,n]       the Sec. 4.2 synthetic study (Table 4.1): both forms, bf16 / fp16 / fp32
                         inner precisions and the FP64 solver over the eight q, n = 100 and 1000
     batched:<count>     <count> random stable equations, n log-uniform in [64, 1024], rank 1..8,
@@ -450,6 +451,12 @@ def run_case(args):
         H = torch.tensor((T * P[None, :]) @ T.T, device=dev)
         for _ in range(2):
             lyap.sym_eig(H, refine=True)
+    elif kind == "lowrank":
+        import lyapgen
+        n, q, u = int(rest[0]), float(rest[1]), rest[2]
+        d = lyapgen.paper_synthetic(n, q)
+        fn = lyap.sign_solve if u == "fp64" else lyap.solve_ir
+        fn(torch.tensor(d["A"], device=dev), torch.tensor(d["L"], device=dev), u_s=u, tau_ir=TAU)
     elif kind == "solve":
         d = make_problem()
         lyap.solve_ir(torch.tensor(d["A"], device=dev), torch.tensor(d["L"], device=dev), u_s=rest[0], tau_ir=TAU,

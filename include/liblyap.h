@@ -255,7 +255,8 @@ int lyap_trace_loss(lyap_ctx_t* ctx, const double* Z, int64_t n, int64_t ldz, in
  *             7 bits; digit products are exact in the FP32 accumulators (K in chunks of 1024)
  *             and the 36 leading pairs are summed in FP64.  Error about 2^-50 K max|a| max|b|
  *             per entry (row / column maxima), the order of an FP64 product's bound.
- *   method 0: 2 for products of at least 3e7 multiply-adds, 1 below.
+ *   method 0: 2 for products of at least 3e7 multiply-adds with k >= 128 and at least 48
+ *             output tiles of 128 x 32, 1 otherwise.
  * Synchronises the context stream; returns LYAP_ERR_TIMEOUT if a bounded device wait gave up.
  */
 int lyap_dgemm(lyap_ctx_t* ctx, char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,

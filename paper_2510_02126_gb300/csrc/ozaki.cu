@@ -20,13 +20,17 @@
 
 namespace lyap {
 
-constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 64, OZ_STAGES = 4;
+constexpr int OZ_BM = 128, OZ_BN = 32, OZ_BK = 64, OZ_STAGES = 4;
 constexpr int OZ_A_BYTES = OZ_BM * OZ_BK * 2;  // 16 KB
-constexpr int OZ_B_BYTES = OZ_BN * OZ_BK * 2;  // 8 KB
+constexpr int OZ_B_BYTES = OZ_BN * OZ_BK * 2;  // 4 KB
 constexpr int OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;
 constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE_BYTES + 1024 + 256;
 constexpr int OZ_NPAIRS = OZ_SLICES * (OZ_SLICES + 1) / 2;  // pairs with s + t <= S + 1 (s, t >= 1)
-constexpr int OZ_THREADS = 160;                             // 4 epilogue warps + 1 producer warp
+constexpr int OZ_THREADS = 192;                             // 4 epilogue warps, MMA warp, TMA warp
+constexpr int OZ_FP32_LEVEL = 5;                             // 0-based s + t summed in FP32 from here
+// pairs at levels >= OZ_FP32_LEVEL (they come first in the descending order)
+constexpr int OZ_NPAIRS_FP32 = OZ_NPAIRS - OZ_FP32_LEVEL * (OZ_FP32_LEVEL + 1) / 2;
+static_assert(OZ_NPAIRS_FP32 == 21, "levels 5, 6, 7 of eight slices");
 
 // ---------------------------------------------------------------------------
 // split
@@ -127,7 +131,6 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   uint64_t* accfull = empty + OZ_STAGES;  // [2]
   uint64_t* accempty = accfull + 2;       // [2]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accempty + 2);
-  __shared__ int fail_s;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.y * OZ_BM, n0 = blockIdx.x * OZ_BN;
   const int nchunk = (nkb + OZ_KCHUNK / OZ_BK - 1) / (OZ_KCHUNK / OZ_BK);
@@ -142,7 +145,6 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       mbar_init(&accfull[b], 1);
       mbar_init(&accempty[b], 4);
     }
-    fail_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(tmem_slot, 2 * OZ_BN);
@@ -151,37 +153,49 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 4) {
-    // ---------------- producer: TMA loads and MMA issue (one thread) ----------------
+  if (warp >= 4) {
     // Iteration `it` is one k-block of one accumulation (chunk, pair); chunks are full
-    // (OZ_KCHUNK / OZ_BK k-blocks) but the last.  Loads run OZ_STAGES iterations ahead.
-    if (lane == 0) {
-      constexpr int KBC = OZ_KCHUNK / OZ_BK;
-      const int per_chunk = KBC * OZ_NPAIRS;
-      const int last_len = nkb - (nchunk - 1) * KBC;
-      const int total_it = (nchunk - 1) * per_chunk + last_len * OZ_NPAIRS;
-      auto decode = [&](int x, int& pi, int& kb, int& first, int& last) {
-        const int c = min(x / per_chunk, nchunk - 1);
-        const int off = x - c * per_chunk;
-        const int len = (c == nchunk - 1) ? last_len : KBC;
-        pi = off / len;
-        const int kk = off - pi * len;
-        kb = c * KBC + kk;
-        first = (kk == 0);
-        last = (kk == len - 1);
-      };
-      auto issue = [&](int x) {
+    // (OZ_KCHUNK / OZ_BK k-blocks) but the last.  Warp 5 (one lane) streams the digit tiles
+    // by TMA into the ring as stages free up; warp 4 (one lane) waits for each stage and
+    // issues its MMAs -- the two never wait for each other's latency.
+    constexpr int KBC = OZ_KCHUNK / OZ_BK;
+    const int per_chunk = KBC * OZ_NPAIRS;
+    const int last_len = nkb - (nchunk - 1) * KBC;
+    const int total_it = (nchunk - 1) * per_chunk + last_len * OZ_NPAIRS;
+    auto decode = [&](int x, int& pi, int& kb, int& first, int& last) {
+      const int c = min(x / per_chunk, nchunk - 1);
+      const int off = x - c * per_chunk;
+      const int len = (c == nchunk - 1) ? last_len : KBC;
+      pi = off / len;
+      const int kk = off - pi * len;
+      kb = c * KBC + kk;
+      first = (kk == 0);
+      last = (kk == len - 1);
+    };
+    if (warp == 5 && lane == 0) {
+      // ---------------- TMA producer ----------------
+      bool ok = true;
+      int issued = 0;
+      for (; issued < total_it; ++issued) {
+        const int st = issued % OZ_STAGES;
+        const unsigned ph = (unsigned)(issued / OZ_STAGES) & 1u;
+        if (issued >= OZ_STAGES && !mbar_wait(&empty[st], ph ^ 1u)) { ok = false; break; }
         int pi, kb, f, l;
-        decode(x, pi, kb, f, l);
-        const int st = x % OZ_STAGES;
+        decode(issued, pi, kb, f, l);
         unsigned char* sa = base + st * OZ_STAGE_BYTES;
         mbar_expect_tx(&full[st], OZ_STAGE_BYTES);
         tma_load_2d(sa, &tmA, kb * OZ_BK, (int)(c_oz_pairs.s[pi] * Mp + m0), &full[st]);
         tma_load_2d(sa + OZ_A_BYTES, &tmB, kb * OZ_BK, (int)(c_oz_pairs.t[pi] * Np + n0), &full[st]);
-      };
+      }
+      if (!ok) {
+        atomicCAS(status, 0, LYAP_ERR_TIMEOUT);
+        // let the copies in flight land before the CTA exits (bounded waits)
+        for (int x = max(0, issued - OZ_STAGES); x < issued; ++x)
+          (void)mbar_wait(&full[x % OZ_STAGES], (unsigned)(x / OZ_STAGES) & 1u);
+      }
+    } else if (warp == 4 && lane == 0) {
+      // ---------------- MMA issuer ----------------
       const uint32_t idesc = make_idesc_mn(0, OZ_BM, OZ_BN);
-      int issued = 0;
-      for (; issued < total_it && issued < OZ_STAGES; ++issued) issue(issued);
       bool ok = true;
       int a = -1;  // current accumulation
       for (int it = 0; it < total_it; ++it) {
@@ -204,40 +218,51 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         for (int kk = 0; kk < OZ_BK / 16; ++kk) tc_mma(dcol, ad + 2 * kk, bd + 2 * kk, idesc, (!first || kk > 0) ? 1 : 0);
         tc_commit(&empty[st]);
         if (last) tc_commit(&accfull[a & 1]);
-        // refill this stage with the load OZ_STAGES iterations ahead once its MMAs are done
-        if (issued < total_it) {
-          if (!mbar_wait(&empty[st], ph)) { ok = false; break; }
-          issue(issued);
-          ++issued;
-        }
       }
-      if (!ok) {
-        atomicCAS(status, 0, LYAP_ERR_TIMEOUT);
-        fail_s = 1;
-        // let the copies in flight land before the CTA exits (bounded waits)
-        for (int x = max(0, issued - OZ_STAGES); x < issued; ++x)
-          (void)mbar_wait(&full[x % OZ_STAGES], (unsigned)(x / OZ_STAGES) & 1u);
-      }
+      if (!ok) atomicCAS(status, 0, LYAP_ERR_TIMEOUT);
     }
   } else {
     // ---------------- epilogue warps 0..3: TMEM lanes 32 w .. 32 w + 31 ----------------
+    // The pairs of the deepest levels (0-based s + t >= OZ_FP32_LEVEL) are summed in FP32,
+    // relative to 2^(-OZ_BETA (OZ_FP32_LEVEL + 2)): their rounding stays below 2^-55 K of the
+    // row / column scale, and the FP64 pipe (narrow on this GPU) takes only the leading pairs.
     double acc[OZ_BN];
+    float acc32[OZ_BN];
 #pragma unroll
-    for (int j = 0; j < OZ_BN; ++j) acc[j] = 0.0;
+    for (int j = 0; j < OZ_BN; ++j) { acc[j] = 0.0; acc32[j] = 0.f; }
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     bool ok = true;
     for (int a = 0; a < total; ++a) {
       const int pi = a % OZ_NPAIRS;
       const int b = a & 1, use = a >> 1;
+      const int lev = c_oz_pairs.s[pi] + c_oz_pairs.t[pi];
       if (!mbar_wait(&accfull[b], (unsigned)use & 1u)) { ok = false; break; }
       tc_fence_after();
-      const double sc = ldexp(1.0, -OZ_BETA * (c_oz_pairs.s[pi] + c_oz_pairs.t[pi] + 2));
+      if (lev >= OZ_FP32_LEVEL) {
+        const float sc = ldexpf(1.f, -OZ_BETA * (lev - OZ_FP32_LEVEL));
 #pragma unroll
-      for (int j0 = 0; j0 < OZ_BN; j0 += 16) {
-        float v[16];
-        tmem_ld16(lane_base + (uint32_t)(b * OZ_BN + j0), v);
+        for (int j0 = 0; j0 < OZ_BN; j0 += 16) {
+          float v[16];
+          tmem_ld16(lane_base + (uint32_t)(b * OZ_BN + j0), v);
 #pragma unroll
-        for (int u = 0; u < 16; ++u) acc[j0 + u] = fma(sc, (double)v[u], acc[j0 + u]);
+          for (int u = 0; u < 16; ++u) acc32[j0 + u] = fmaf(sc, v[u], acc32[j0 + u]);
+        }
+      } else {
+        if (pi == OZ_NPAIRS_FP32) {  // first FP64 pair of this chunk: fold the FP32 sum in
+#pragma unroll
+          for (int j = 0; j < OZ_BN; ++j) {
+            acc[j] += ldexp((double)acc32[j], -OZ_BETA * (OZ_FP32_LEVEL + 2));
+            acc32[j] = 0.f;
+          }
+        }
+        const double sc = ldexp(1.0, -OZ_BETA * (lev + 2));
+#pragma unroll
+        for (int j0 = 0; j0 < OZ_BN; j0 += 16) {
+          float v[16];
+          tmem_ld16(lane_base + (uint32_t)(b * OZ_BN + j0), v);
+#pragma unroll
+          for (int u = 0; u < 16; ++u) acc[j0 + u] = fma(sc, (double)v[u], acc[j0 + u]);
+        }
       }
       tc_fence_before();
       __syncwarp();

@@ -82,6 +82,33 @@ def test_ir_ldlt_indefinite(u_s, p):
     assert rel((Z * D) @ Z.T, X) <= 1e-10
 
 
+def test_ir_ldlt_bf16_normal_blocks_stalls_like_oracle():
+    # the input on which BF16 inner solves cannot converge (the oracle's BF16 emulation stalls
+    # as well, tests/test_oracle_pins.py): the GPU refinement stops by the stagnation rule with
+    # a residual of the oracle's order, far above the FP64 limit
+    d = gen.normal_blocks(n=128, p=1, m=4)
+    A, L, S = d["A"], d["L"], d["S"]
+    Z, D, info = lib().solve_ir(T(A), T(L), S=T(S), u_s="bf16", tau_ir=1e-12, imax=20)
+    assert not info.converged and info.status in (lib().WARN_STAGNATED, lib().WARN_MAXIT), info.as_dict()
+    Zo, yo, oinfo = O.ir_ldlt(A, L, S, O.Opts(u_s="bf16", tau_ir=1e-12, imax=20))
+    assert not oinfo.converged
+    assert 0.1 <= info.res_final / oinfo.res_final <= 10.0, (info.res_final, oinfo.res_final)
+
+
+def test_ir_ldlt_indefinite_n1024_fp32():
+    # LDL^T form at n = 1024 (indefinite S, normal blocks, p = 1) with FP32 inner solves,
+    # against the Schur-block closed form of the exact solution
+    from tests.test_oracle_pins import schur_blocks_solution
+    d = gen.normal_blocks(n=1024, p=1, m=8, indefinite=True)
+    A, L, S = d["A"], d["L"], d["S"]
+    W = L @ S @ L.T
+    Z, D, info = lib().solve_ir(T(A), T(L), S=T(S), u_s="fp32", tau_ir=1e-12, imax=20)
+    assert info.converged, info.as_dict()
+    X = schur_blocks_solution(d["Q"], d["alpha"], d["beta"], W)
+    assert rel((N(Z) * N(D)) @ N(Z).T, X) <= 1e-10
+    assert O.residual_eq41(A, N(Z), W, N(D)) <= 1e-12
+
+
 def test_ir_ldlt_bf16_synthetic():
     # bf16 needs a mild problem (Table 4.1: bf16 converges up to cond ~1e2 at n = 100);
     # on the normal-block family with Re(lambda) down to -0.1 the oracle stalls as well
@@ -111,6 +138,21 @@ def test_ir_config_convdiff_1024_fp16():
     Z = N(Z)
     res = O.residual_eq41(A, Z, W)
     assert info.converged and res <= 1e-12, (res, info.as_dict())
+    X = O.bartels_stewart(A, W)
+    assert rel(Z @ Z.T, X) <= 1e-10
+
+
+def test_ir_config_convdiff_1024_bf16():
+    # the BF16 variant of the n = 1024 workload: kappa ~ 1e3 is at the Table 2.1 bound of
+    # bf16, so the refinement contracts slowly (about x0.5 per step) but reaches 1e-12
+    d = gen.convdiff_shifted()
+    A, L = d["A"], d["L"]
+    W = L @ L.T
+    Z, _, info = lib().solve_ir(T(A), T(L), u_s="bf16", tau_ir=1e-12, imax=50)
+    Z = N(Z)
+    res = O.residual_eq41(A, Z, W)
+    assert info.converged and res <= 1e-12, (res, info.as_dict())
+    assert info.n_inversions == info.newton_max
     X = O.bartels_stewart(A, W)
     assert rel(Z @ Z.T, X) <= 1e-10
 

@@ -400,6 +400,16 @@ def test_ir_stagnation_beyond_bf16_bound():
     assert not info.converged
 
 
+def test_ir_ldlt_bf16_stalls_on_normal_blocks():
+    # A = Q T Q^T with 2 x 2 blocks -a +- i b (b up to 5, a down to 0.1): eigenvalues close to
+    # the imaginary axis relative to their size put the problem beyond bf16's reach (Table 2.1);
+    # the BF16-inner refinement does not contract and the stagnation rule stops it
+    d = gen.normal_blocks(n=128, p=1, m=4)
+    Z, y, info = O.ir_ldlt(d["A"], d["L"], d["S"], O.Opts(u_s="bf16", tau_ir=1e-12, imax=20))
+    assert not info.converged and info.stagnated
+    assert min(info.res_hist) > 1e-3
+
+
 # ---------------------------------------------------------------- adjoint
 
 def test_adjoint_vs_kronecker_bruteforce():
