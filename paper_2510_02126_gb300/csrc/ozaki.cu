@@ -35,39 +35,59 @@ static_assert(OZ_NPAIRS_FP32 == 21, "levels 5, 6, 7 of eight slices");
 // ---------------------------------------------------------------------------
 // split
 // ---------------------------------------------------------------------------
-// e[r] = exponent with max_l |x(r, l)| < 2^e[r] (0 for a zero row); x(r, l) = X[r + l ld]
-// (tr = 0) or X[l + r ld] (tr = 1)
-__global__ void oz_rowexp_kernel(const double* __restrict__ X, int64_t ld, int tr, int64_t R, int64_t K,
-                                 int* __restrict__ e) {
+// The split runs in integer arithmetic on the bit patterns (FP64 operations are scarce on
+// this GPU and would cost as much as the product).
+constexpr int OZ_NO_EXP = (int)0x80808080;  // byte-wise memset sentinel: the row is zero
+
+// frexp exponent of |x| from its bits (|x| < 2^result); OZ_NO_EXP for zero
+__device__ __forceinline__ int oz_exponent(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+  if (b == 0) return OZ_NO_EXP;
+  const int E = (int)(b >> 52);
+  return (E == 0 ? 1 : E) - 1022;
+}
+
+// e[r] = max over the row of the exponents (max_l |x(r, l)| < 2^e[r]); e must hold OZ_NO_EXP
+// on entry.  x(r, l) = X[r + l ld] (tr = 0) or X[l + r ld] (tr = 1).  One 32 x 32 tile per
+// CTA, loads coalesced along the contiguous index, one atomicMax per row and tile.
+__global__ void __launch_bounds__(256) oz_rowexp_kernel(const double* __restrict__ X, int64_t ld, int tr, int64_t R,
+                                                        int64_t K, int* __restrict__ e) {
+  __shared__ int m[8][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, l0 = (int64_t)blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   if (tr == 0) {
-    // thread per row: consecutive rows are contiguous, so every step of l is coalesced
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= R) return;
-    double m = 0.0;
-    for (int64_t l = 0; l < K; ++l) m = fmax(m, fabs(X[r + l * ld]));
-    int ex = 0;
-    if (m > 0.0) frexp(m, &ex);
-    e[r] = ex;
+    // thread tx <-> row r0 + tx (contiguous), columns l0 + ty + 8 k
+    const int64_t r = r0 + tx;
+    int mx = OZ_NO_EXP;
+    for (int k = ty; k < 32; k += 8) {
+      const int64_t l = l0 + k;
+      if (r < R && l < K) mx = max(mx, oz_exponent(X[r + l * ld]));
+    }
+    m[ty][tx] = mx;
+    __syncthreads();
+    if (ty == 0 && r < R) {
+      for (int u = 1; u < 8; ++u) mx = max(mx, m[u][tx]);
+      if (mx != OZ_NO_EXP) atomicMax(&e[r], mx);
+    }
   } else {
-    // warp per row: the row is contiguous
-    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (r >= R) return;
-    double m = 0.0;
-    for (int64_t l = lane; l < K; l += 32) m = fmax(m, fabs(X[l + r * ld]));
-    m = warp_max(m);
-    if (lane == 0) {
-      int ex = 0;
-      if (m > 0.0) frexp(m, &ex);
-      e[r] = ex;
+    // warp ty <-> rows r0 + ty + 8 k, lane tx <-> column l0 + tx (contiguous)
+    for (int k = ty; k < 32; k += 8) {
+      const int64_t r = r0 + k, l = l0 + tx;
+      int v = (r < R && l < K) ? oz_exponent(X[l + r * ld]) : OZ_NO_EXP;
+      v = __reduce_max_sync(0xffffffffu, v);
+      if (tx == 0 && r < R && v != OZ_NO_EXP) atomicMax(&e[r], v);
     }
   }
 }
 
-// digits of the 32 x 32 tile (rows r0.., columns l0..) into the slices (zeros in the padding)
+// digits of the 32 x 32 tile (rows r0.., columns l0..) into the slices (zeros in the padding):
+// A = round(|x| 2^(56 - e)) as a 64-bit integer (|A| <= 2^56), then balanced base-2^OZ_BETA
+// digits from the top: d = round(A / 2^sh), A -= d 2^sh, sh = 56 - OZ_BETA s.  Exact:
+// x = 2^(e - 56) sum_s d_s 2^(56 - OZ_BETA s) up to the bits of x below 2^(e - 56).
 __global__ void __launch_bounds__(256) oz_digits_kernel(const double* __restrict__ X, int64_t ld, int tr, int64_t R,
                                                         int64_t K, const int* __restrict__ e, __half* __restrict__ D,
                                                         int64_t Rp, int64_t Kp) {
+  static_assert(OZ_BETA * OZ_SLICES == 56, "digits cover 56 bits below the row exponent");
   __shared__ double t[32][33];
   const int64_t r0 = (int64_t)blockIdx.y * 32, l0 = (int64_t)blockIdx.x * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
@@ -85,13 +105,31 @@ __global__ void __launch_bounds__(256) oz_digits_kernel(const double* __restrict
   for (int k = ty; k < 32; k += 8) {
     const int64_t r = r0 + k, l = l0 + tx;
     if (r >= Rp || l >= Kp) continue;
-    double a = (r < R) ? ldexp(t[k][tx], -e[r]) : 0.0;
+    long long A = 0;
+    const int er = (r < R) ? e[r] : OZ_NO_EXP;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(t[k][tx]);
+    const unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFull;
+    if (er != OZ_NO_EXP && mag != 0) {
+      const int E = (int)(mag >> 52);
+      const unsigned long long mant = (mag & 0x000FFFFFFFFFFFFFull) | (E ? (1ull << 52) : 0ull);
+      const int shift = (E ? E : 1) - 1075 + 56 - er;  // |x| = mant 2^((E ? E : 1) - 1075)
+      unsigned long long a;
+      if (shift >= 0) a = mant << shift;                 // |x| < 2^er: a < 2^56
+      else if (shift > -64) a = (mant + (1ull << (-shift - 1))) >> (-shift);
+      else a = 0;
+      A = (b >> 63) ? -(long long)a : (long long)a;
+    }
 #pragma unroll
-    for (int s = 0; s < OZ_SLICES; ++s) {
-      const double u = a * (double)(1 << OZ_BETA);
-      const double d = rint(u);
-      a = u - d;
-      D[(size_t)s * Rp * Kp + (size_t)r * Kp + l] = __float2half_rn((float)d);  // |d| <= 2^OZ_BETA: exact
+    for (int sl = 0; sl < OZ_SLICES; ++sl) {
+      const int sh = 56 - OZ_BETA * (sl + 1);
+      long long d;
+      if (sh > 0) {
+        d = (A + (1ll << (sh - 1))) >> sh;
+        A -= d << sh;
+      } else {
+        d = A;
+      }
+      D[(size_t)sl * Rp * Kp + (size_t)r * Kp + l] = __int2half_rn((int)d);  // |d| <= 2^OZ_BETA: exact
     }
   }
 }
@@ -271,13 +309,13 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     if (!ok) atomicCAS(status, 0, LYAP_ERR_TIMEOUT);
     const int row = m0 + warp * 32 + lane;
     if (ok && row < M) {
-      const int ea = eA[row];
+      const int ea = max(eA[row], -1100);  // a zero row (no exponent) has acc = 0
 #pragma unroll
       for (int j = 0; j < OZ_BN; ++j) {
         const int col = n0 + j;
         if (col < N) {
           double* c = C + (size_t)row + (size_t)col * ldc;
-          const double v = alpha * ldexp(acc[j], ea + eB[col]);
+          const double v = alpha * ldexp(acc[j], ea + max(eB[col], -1100));
           *c = (beta == 0.0) ? v : fma(beta, *c, v);
         }
       }
@@ -321,9 +359,9 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 int oz_split(const double* X, int64_t ld, int tr, int64_t R, int64_t K, int64_t Rp, int64_t Kp, int* e, __half* D,
              cudaStream_t s) {
-  if (tr == 0) oz_rowexp_kernel<<<(unsigned)ceil_div(R, 128), 128, 0, s>>>(X, ld, 0, R, K, e);
-  else oz_rowexp_kernel<<<(unsigned)ceil_div(R * 32, 256), 256, 0, s>>>(X, ld, 1, R, K, e);
+  LYAP_CUDA_TRY(cudaMemsetAsync(e, 0x80, sizeof(int) * (size_t)Rp, s));  // OZ_NO_EXP
   dim3 g((unsigned)(Kp / 32), (unsigned)(Rp / 32));
+  oz_rowexp_kernel<<<g, 256, 0, s>>>(X, ld, tr, R, K, e);
   oz_digits_kernel<<<g, 256, 0, s>>>(X, ld, tr, R, K, e, D, Rp, Kp);
   LYAP_CUDA_TRY(cudaGetLastError());
   lyap_count_launch(2);
