@@ -91,6 +91,10 @@ typedef struct {
   int fp64_products;    /* FP64 matrix products of the refinement: 0 = library's choice (emulated
                            on the FP16 tensor cores above a size threshold), 1 = FP64 SIMT,
                            2 = always emulated (see lyap_dgemm) */
+  int u, u_r, u_c;      /* lyap_prec_t of the working precision, of the residual and of the
+                           solution update (Algorithms IR-Chol / IR-LDLT, Table 2.1): this
+                           library implements u = u_r = u_c = LYAP_FP64 (the configuration the
+                           analysis of Sec. 2 targets); any other value returns LYAP_ERR_ARG */
   int reserved[3];
 } lyap_opts_t;
 

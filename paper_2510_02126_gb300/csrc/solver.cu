@@ -1496,6 +1496,10 @@ static int check_problem(const Problem& pb, const lyap_opts_t* o, double* Z, int
   if (pb.n <= 0 || pb.m <= 0 || pb.lda < pb.n || pb.ldl < pb.n || ldz < pb.n || z_cap <= 0) return LYAP_ERR_ARG;
   if (pb.S && pb.lds < pb.m) return LYAP_ERR_ARG;
   if (o->u_s < 0 || o->u_s > 3 || o->scaling < 0 || o->scaling > 2 || o->kmax <= 0 || o->imax < 0) return LYAP_ERR_ARG;
+  if (o->u != LYAP_FP64 || o->u_r != LYAP_FP64 || o->u_c != LYAP_FP64) {
+    lyap_set_error_message("only u = u_r = u_c = LYAP_FP64 is implemented", __FILE__, __LINE__);
+    return LYAP_ERR_ARG;
+  }
   return LYAP_OK;
 }
 
@@ -1705,6 +1709,7 @@ static int adjoint_entry(lyap_ctx_t* Cp, const double* A, int64_t n, int64_t lda
                          double* dA, int64_t ldda, double* dL, int64_t lddl, double* dS, int64_t ldds, double* Zy,
                          int64_t ldzy, int64_t zy_cap, int64_t* rank_y, lyap_info_t* info) {
   if (!Cp || !A || !L || !Z || !Cm || !opts || n <= 0 || m <= 0 || r < 0 || q <= 0) return LYAP_ERR_ARG;
+  if (opts->u != LYAP_FP64 || opts->u_r != LYAP_FP64 || opts->u_c != LYAP_FP64) return LYAP_ERR_ARG;
   if (lda < n || ldl < n || ldz < n || ldc < q || (S && lds < m)) return LYAP_ERR_ARG;
   if ((dA && ldda < n) || (dL && lddl < n) || (dS && ldds < m) || (Zy && (ldzy < n || !rank_y))) return LYAP_ERR_ARG;
   Ctx& C = *Cp;

@@ -36,7 +36,7 @@ class LyapOpts(C.Structure):
         ("rho", C.c_double), ("kmax", C.c_int), ("imax", C.c_int), ("tau_ir", C.c_double), ("eta_r", C.c_double),
         ("eta_s", C.c_double), ("stag_theta", C.c_double), ("stag_count", C.c_int), ("project_psd", C.c_int),
         ("profile", C.c_int), ("ckpt_every", C.c_int), ("mem_budget", C.c_int64), ("fp64_products", C.c_int),
-        ("reserved", C.c_int * 3),
+        ("u", C.c_int), ("u_r", C.c_int), ("u_c", C.c_int), ("reserved", C.c_int * 3),
     ]
 
 

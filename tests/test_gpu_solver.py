@@ -191,6 +191,16 @@ def test_capacity_error():
     assert getattr(ei.value, "status", None) == lib().ERR_CAPACITY
 
 
+def test_working_precisions_other_than_fp64_rejected():
+    # u = u_r = u_c = FP64 is the implemented configuration (Table 2.1, bottom half)
+    d = gen.convdiff_shifted(grid=5, m=2)
+    for field in ("u", "u_r", "u_c"):
+        o = lib().make_opts("fp16", **{field: lib().FP32})
+        with pytest.raises(Exception) as ei:
+            lib().solve_ir(T(d["A"]), T(d["L"]), opts=o)
+        assert getattr(ei.value, "status", None) == lib().ERR_ARG
+
+
 def test_nonfinite_input():
     d = gen.convdiff_shifted(grid=5, m=2)
     A = d["A"].copy()
