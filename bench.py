@@ -367,11 +367,18 @@ def run_ours(args):
         "eig_refine": ("alu", 1.25, "nominal FP64 1.25 TFLOP/s (GB300)",
                        "gemm_kernel<double> (Ogita-Aishima refinement, Newton-Schulz)", "2 m n k flop per GEMM"),
     }
+    # DRAM traffic per launch of a phase's dominant kernel, from one ncu capture of this
+    # workload (null where no capture of the current kernel exists)
+    traffic = {"eig": (4.6963e6, "DRAM bytes read + written per bjac_kernel launch, mean of the 36 launches of one "
+                                 "solve (profiles/bjac_kernel_convdiff1024_dram.md)")}
+
     def roof(k):
         bound, peak, peak_kind, kern, work = kinds[k]
         ach = flops[k] / (phase[k] * 1e-3) / 1e12 if phase[k] > 0 else 0.0
+        tr = traffic.get(k)
         return {"kernel": kern, "phase": k, "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak if peak else None, "traffic": None, "peak_kind": peak_kind,
+                "frac": ach / peak if peak else None, "traffic": tr[0] if tr else None,
+                "traffic_kind": tr[1] if tr else None, "peak_kind": peak_kind,
                 "work": f"{work}; {flops[k]:.3e} flop and {phase[k]:.1f} ms per solve in this phase"}
     dom = max(phase, key=phase.get)
     dom_k = max(kinds, key=lambda k: phase[k])
@@ -420,6 +427,8 @@ def run_case(args):
                         residual cores of the refinement
     solve:<u_s>         one lyap_solve_ir of the benchmark workload
     lowrank:<n>:<q>:<u> one solve of the Sec. 4.2 family (IR at u, or the FP64 sign-Newton for fp64)
+    time_invert:<n,..>  lyap_invert at every precision (CUDA events; one JSON line each)
+    time_dgemm          lyap_dgemm, FP64 SIMT against the tensor-core emulation (one JSON line per shape)
     table41[:n,n]       the Sec. 4.2 synthetic study (Table 4.1): both forms, bf16 / fp16 / fp32
                         inner precisions and the FP64 solver over the eight q, n = 100 and 1000
     batched:<count>     <count> random stable equations, n log-uniform in [64, 1024], rank 1..8,
@@ -451,6 +460,52 @@ def run_case(args):
         H = torch.tensor((T * P[None, :]) @ T.T, device=dev)
         for _ in range(2):
             lyap.sym_eig(H, refine=True)
+    elif kind == "time_invert":
+        # lyap_invert at every precision, CUDA events over 5 calls after 2 warm-up calls
+        stream = torch.cuda.current_stream()
+        for n in [int(x) for x in rest[0].split(",")]:
+            A = torch.tensor(g.standard_normal((n, n)) + 2.0 * np.sqrt(n) * np.eye(n), device=dev)
+            for prec in ("fp16", "bf16", "fp32", "fp64"):
+                for _ in range(2):
+                    lyap.invert(A, prec)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(5):
+                    Ai, _, _ = lyap.invert(A, prec)
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1) / 5
+                err = float((Ai @ A - torch.eye(n, device=dev, dtype=torch.float64)).abs().max())
+                print(json.dumps({"case": "time_invert", "n": n, "prec": prec, "ms": ms,
+                                  "tflops_2n3": 2 * n ** 3 / ms / 1e9, "max_abs_AXminusI": err}), flush=True)
+        return 0
+    elif kind == "time_dgemm":
+        # lyap_dgemm, FP64 SIMT against the FP16 tensor-core emulation, on the shapes of the
+        # refinement (A Z, the core products, the eigen refinement) and a square one
+        stream = torch.cuda.current_stream()
+        for (m, n, k, ta, tb) in ((1024, 421, 1024, "N", "N"), (846, 846, 846, "N", "T"), (900, 900, 900, "T", "N"),
+                                  (4096, 281, 4096, "N", "N"), (2048, 2048, 2048, "N", "N")):
+            A = torch.tensor(g.standard_normal((k, m) if ta == "T" else (m, k)), device=dev)
+            B = torch.tensor(g.standard_normal((n, k) if tb == "T" else (k, n)), device=dev)
+            rec = {"case": "time_dgemm", "m": m, "n": n, "k": k, "op": ta + tb}
+            outs = {}
+            for meth in ("simt", "tensor"):
+                C = lyap.dgemm(A, B, ta, tb, method=meth)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(5):
+                    C = lyap.dgemm(A, B, ta, tb, C=C, method=meth)
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1) / 5
+                rec[meth + "_ms"] = ms
+                rec[meth + "_fp64_tflops"] = 2 * m * n * k / ms / 1e9
+                outs[meth] = C
+            rec["max_rel_diff"] = float((outs["simt"] - outs["tensor"]).abs().max() / outs["simt"].abs().max())
+            print(json.dumps(rec), flush=True)
+        return 0
     elif kind == "lowrank":
         import lyapgen
         n, q, u = int(rest[0]), float(rest[1]), rest[2]
