@@ -485,7 +485,9 @@ def run_case(args):
         # refinement (A Z, the core products, the eigen refinement) and a square one
         stream = torch.cuda.current_stream()
         for (m, n, k, ta, tb) in ((1024, 421, 1024, "N", "N"), (846, 846, 846, "N", "T"), (900, 900, 900, "T", "N"),
-                                  (4096, 281, 4096, "N", "N"), (2048, 2048, 2048, "N", "N")):
+                                  (4096, 281, 4096, "N", "N"), (2048, 2048, 2048, "N", "N"),
+                                  (281, 281, 4096, "T", "N"), (4096, 32, 4096, "N", "N"), (421, 421, 1024, "T", "N"),
+                                  (128, 128, 4096, "T", "N")):
             A = torch.tensor(g.standard_normal((k, m) if ta == "T" else (m, k)), device=dev)
             B = torch.tensor(g.standard_normal((n, k) if tb == "T" else (k, n)), device=dev)
             rec = {"case": "time_dgemm", "m": m, "n": n, "k": k, "op": ta + tb}

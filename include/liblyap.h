@@ -314,9 +314,12 @@ int lyap_rank_trunc(lyap_ctx_t* ctx, double* Z, int64_t n, int64_t c, int64_t ld
  * Symmetric eigendecomposition H = Q diag(w) Q^T of a q x q FP64 matrix (the kernel
  * behind Fragments ResFacChol / SolUptChol): H (ldh >= q, overwritten), w (q, ascending),
  * Q (q x q, ldq >= q).  All device pointers.  fp64_refine = 1 refines the eigenpairs
- * to FP64 accuracy; 0 returns the FP32-accurate result.  Orders up to 1280 (the block
- * Jacobi uses one CTA per pair of 8-index blocks, all resident: q / 16 CTAs, twice that
- * when the GPU has the SMs); larger q returns LYAP_ERR_ARG before any launch.
+ * to FP64 accuracy; 0 returns the FP32-accurate result.  Up to order 1280 one block
+ * Jacobi launch (one CTA per pair of 8-index blocks, all resident: q / 16 CTAs, twice
+ * that when the GPU has the SMs); above it Jacobi over super-blocks of at most 512
+ * indices whose pairs that kernel diagonalises (FP32 products update the rest), then the
+ * same refinement.  Orders above 32768 return LYAP_ERR_ARG before any launch.  Scratch
+ * grows to about 18 q^2 floats for q > 1280.
  */
 int lyap_sym_eig(lyap_ctx_t* ctx, double* H, int64_t q, int64_t ldh, double* w, double* Q,
                  int64_t ldq, int fp64_refine);

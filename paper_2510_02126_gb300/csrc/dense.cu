@@ -103,9 +103,11 @@ int dgemm_method() { return g_dgemm_method; }
 static bool use_tensor_fp64(int64_t M, int64_t N, int64_t K) {
   if (g_dgemm_method == DGEMM_SIMT) return false;
   if (g_dgemm_method == DGEMM_TENSOR) return true;
-  // enough work, a K worth the digit split, and enough 128 x 32 tiles to occupy the GPU
+  // enough work, a K worth the digit split, and enough (128 x 32 tile, K split) pairs to occupy
+  // the GPU: ozaki_dgemm splits K into up to 16 ranges of at least 256 when tiles are few
   const int64_t tiles = ceil_div(M, 128) * ceil_div(N, 32);
-  return (double)M * (double)N * (double)K >= OZ_MIN_MACS && K >= 128 && tiles >= 48;
+  const int64_t splits = std::max<int64_t>(1, std::min<int64_t>(16, K / 256));
+  return (double)M * (double)N * (double)K >= OZ_MIN_MACS && K >= 128 && tiles * splits >= 48;
 }
 
 // C[j, i] = C[i, j] for i < j (the upper triangle of a symmetric product is the result)

@@ -5,10 +5,13 @@
 
 namespace lyap {
 
-constexpr int EIG_MAX_Q = 1280;  // largest order sym_eig accepts (block Jacobi round-robin tables)
+// largest order of the block Jacobi (its round-robin tables); above it sym_eig runs Jacobi over
+// super-blocks whose pairs the block Jacobi diagonalises
+constexpr int EIG_MAX_Q = 1280;
 
 struct EigScratch {
   float* work32 = nullptr;   // bjac_work_floats(q) floats (block Jacobi workspace)
+  float* big = nullptr;      // eig_big_floats(q) floats (orders above EIG_MAX_Q only)
   double* X = nullptr;       // q^2 each
   double* R = nullptr;
   double* S = nullptr;
@@ -48,5 +51,7 @@ int sym_eig(const double* H, int64_t q, int64_t ldh, double* w, double* Q, int64
 
 // Floats of EigScratch::work32 that sym_eig needs for order q (block Jacobi for q > 160).
 size_t bjac_work_floats(int q);
+// Floats of EigScratch::big that sym_eig needs for order q (0 up to EIG_MAX_Q).
+size_t eig_big_floats(int64_t q);
 
 }  // namespace lyap

@@ -27,6 +27,8 @@ constexpr int OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;
 constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE_BYTES + 1024 + 256;
 constexpr int OZ_NPAIRS = OZ_SLICES * (OZ_SLICES + 1) / 2;  // pairs with s + t <= S + 1 (s, t >= 1)
 constexpr int OZ_THREADS = 192;                             // 4 epilogue warps, MMA warp, TMA warp
+constexpr int64_t OZ_TARGET_CTAS = 148;                      // split K until about one CTA per SM
+constexpr int64_t OZ_MAX_SPLIT = 16;
 constexpr int OZ_FP32_LEVEL = 5;                             // 0-based s + t summed in FP32 from here
 // pairs at levels >= OZ_FP32_LEVEL (they come first in the descending order)
 constexpr int OZ_NPAIRS_FP32 = OZ_NPAIRS - OZ_FP32_LEVEL * (OZ_FP32_LEVEL + 1) / 2;
@@ -160,8 +162,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 __global__ void __launch_bounds__(OZ_THREADS, 1)
 oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
-               int64_t Mp, int64_t Np, int nkb, const int* __restrict__ eA, const int* __restrict__ eB, double alpha,
-               double beta, double* __restrict__ C, int64_t ldc, int* status) {
+               int64_t Mp, int64_t Np, int nkb_all, int kbs, const int* __restrict__ eA, const int* __restrict__ eB,
+               double alpha, double beta, double* __restrict__ C, int64_t ldc, double* __restrict__ part, int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(base + OZ_STAGES * OZ_STAGE_BYTES);
@@ -171,8 +173,11 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accempty + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.y * OZ_BM, n0 = blockIdx.x * OZ_BN;
-  const int nchunk = (nkb + OZ_KCHUNK / OZ_BK - 1) / (OZ_KCHUNK / OZ_BK);
-  const int total = nchunk * OZ_NPAIRS;  // accumulations (pairs x chunks)
+  // split-K: this CTA takes the k-blocks [kb_lo, kb_lo + nkb) of the product
+  const int kb_lo = blockIdx.z * kbs;
+  const int nkb = max(0, min(nkb_all - kb_lo, kbs));
+  const int nchunk = max(1, (nkb + OZ_KCHUNK / OZ_BK - 1) / (OZ_KCHUNK / OZ_BK));
+  const int total = (nkb > 0) ? nchunk * OZ_NPAIRS : 0;  // accumulations (pairs x chunks)
 
   if (tid == 0) {
     for (int s = 0; s < OZ_STAGES; ++s) {
@@ -199,14 +204,14 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     constexpr int KBC = OZ_KCHUNK / OZ_BK;
     const int per_chunk = KBC * OZ_NPAIRS;
     const int last_len = nkb - (nchunk - 1) * KBC;
-    const int total_it = (nchunk - 1) * per_chunk + last_len * OZ_NPAIRS;
+    const int total_it = (nkb > 0) ? (nchunk - 1) * per_chunk + last_len * OZ_NPAIRS : 0;
     auto decode = [&](int x, int& pi, int& kb, int& first, int& last) {
       const int c = min(x / per_chunk, nchunk - 1);
       const int off = x - c * per_chunk;
       const int len = (c == nchunk - 1) ? last_len : KBC;
       pi = off / len;
       const int kk = off - pi * len;
-      kb = c * KBC + kk;
+      kb = kb_lo + c * KBC + kk;
       first = (kk == 0);
       last = (kk == len - 1);
     };
@@ -310,13 +315,23 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const int row = m0 + warp * 32 + lane;
     if (ok && row < M) {
       const int ea = max(eA[row], -1100);  // a zero row (no exponent) has acc = 0
+      if (part) {
+        // split-K: this split's share of op(A) op(B), summed by oz_reduce_kernel
+        double* pz = part + (size_t)blockIdx.z * Mp * Np;
 #pragma unroll
-      for (int j = 0; j < OZ_BN; ++j) {
-        const int col = n0 + j;
-        if (col < N) {
-          double* c = C + (size_t)row + (size_t)col * ldc;
-          const double v = alpha * ldexp(acc[j], ea + max(eB[col], -1100));
-          *c = (beta == 0.0) ? v : fma(beta, *c, v);
+        for (int j = 0; j < OZ_BN; ++j) {
+          const int col = n0 + j;
+          if (col < N) pz[(size_t)row + (size_t)col * Mp] = ldexp(acc[j], ea + max(eB[col], -1100));
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < OZ_BN; ++j) {
+          const int col = n0 + j;
+          if (col < N) {
+            double* c = C + (size_t)row + (size_t)col * ldc;
+            const double v = alpha * ldexp(acc[j], ea + max(eB[col], -1100));
+            *c = (beta == 0.0) ? v : fma(beta, *c, v);
+          }
         }
       }
     }
@@ -324,6 +339,20 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, 2 * OZ_BN);
+}
+
+// C = alpha sum_z part[z] + beta C, the splits summed in a fixed order (same bits every call)
+__global__ void oz_reduce_kernel(const double* __restrict__ part, int nsplit, int64_t Mp, int64_t Np, int M, int N,
+                                 double alpha, double beta, double* __restrict__ C, int64_t ldc) {
+  const int64_t total = (int64_t)M * N;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t col = e / M, row = e - col * M;
+    double acc = 0.0;
+    for (int z = 0; z < nsplit; ++z) acc += part[(size_t)z * Mp * Np + row + col * Mp];
+    double* c = C + row + col * ldc;
+    const double v = alpha * acc;
+    *c = (beta == 0.0) ? v : fma(beta, *c, v);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -381,10 +410,23 @@ int ozaki_dgemm(char ta, char tb, int64_t M, int64_t N, int64_t K, double alpha,
   // workspace: digit slices of op(A) (S Mp x Kp) and of op(B)^T (S Np x Kp), exponents
   const size_t bA = (size_t)OZ_SLICES * Mp * Kp * 2, bB = (size_t)OZ_SLICES * Np * Kp * 2;
   const size_t bE = (size_t)(Mp + Np) * 4;
-  LYAP_TRY(oz_ensure(bA + bB + bE + 512));
-  __half* DA = static_cast<__half*>(g_oz.p);
-  __half* DB = reinterpret_cast<__half*>(static_cast<char*>(g_oz.p) + bA);
-  int* eA = reinterpret_cast<int*>(static_cast<char*>(g_oz.p) + bA + bB);
+  // split-K when the output has under half a wave of tiles, to about one wave of CTAs with at
+  // least 4 k-blocks a split (measured: with half a wave or more the extra pass over the
+  // partial products costs more than the idle SMs)
+  const int nkb = (int)(Kp / OZ_BK);
+  const int64_t tiles = (Mp / OZ_BM) * (Np / OZ_BN);
+  int nsplit = 1;
+  if (2 * tiles < OZ_TARGET_CTAS) nsplit = (int)std::min<int64_t>({OZ_MAX_SPLIT, nkb / 4, ceil_div(OZ_TARGET_CTAS, tiles)});
+  nsplit = std::max(1, nsplit);
+  const int kbs = (nkb + nsplit - 1) / nsplit;
+  nsplit = (nkb + kbs - 1) / kbs;
+  const size_t bP = (nsplit > 1) ? (size_t)nsplit * Mp * Np * 8 : 0;
+  LYAP_TRY(oz_ensure(bP + bA + bB + bE + 512));
+  double* part = (nsplit > 1) ? static_cast<double*>(g_oz.p) : nullptr;
+  char* base = static_cast<char*>(g_oz.p) + bP;
+  __half* DA = reinterpret_cast<__half*>(base);
+  __half* DB = reinterpret_cast<__half*>(base + bA);
+  int* eA = reinterpret_cast<int*>(base + bA + bB);
   int* eB = eA + Mp;
   // op(A) rows: A[i + l lda] ('N') or A[l + i lda] ('T');
   // op(B)^T rows (= columns of op(B)): B[l + j ldb] ('N') or B[j + l ldb] ('T')
@@ -400,11 +442,17 @@ int ozaki_dgemm(char ta, char tb, int64_t M, int64_t N, int64_t K, double alpha,
   }
   int* st = tc_status_word();
   if (!st) return LYAP_ERR_NOMEM;
-  dim3 grid((unsigned)(Np / OZ_BN), (unsigned)(Mp / OZ_BM));
-  oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM, s>>>(mA, mB, (int)M, (int)N, Mp, Np, (int)(Kp / OZ_BK), eA, eB, alpha,
-                                                   beta, C, ldc, st);
+  dim3 grid((unsigned)(Np / OZ_BN), (unsigned)(Mp / OZ_BM), (unsigned)nsplit);
+  oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM, s>>>(mA, mB, (int)M, (int)N, Mp, Np, nkb, kbs, eA, eB, alpha, beta, C,
+                                                   ldc, part, st);
   LYAP_CUDA_TRY(cudaGetLastError());
   lyap_count_launch();
+  if (part) {
+    oz_reduce_kernel<<<(unsigned)std::min<int64_t>(4096, ceil_div(M * N, 256)), 256, 0, s>>>(part, nsplit, Mp, Np, (int)M,
+                                                                                           (int)N, alpha, beta, C, ldc);
+    LYAP_CUDA_TRY(cudaGetLastError());
+    lyap_count_launch();
+  }
   return LYAP_OK;
 }
 

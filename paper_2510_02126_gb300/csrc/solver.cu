@@ -109,7 +109,7 @@ struct lyap_ctx {
   lyap::Buf At, Ct, ZY, adjT;
   lyap::Buf tl;  // trace loss: C Z and C Z diag(D)
   lyap::Buf Hf;  // FP32 copy of the residual core for its range finder
-  lyap::Buf eigWork32, eigX, eigR, eigS, eigHX, eigE, eigLam, eigRed, eigW, eigPv, eigInt;
+  lyap::Buf eigWork32, eigBig, eigX, eigR, eigS, eigHX, eigE, eigLam, eigRed, eigW, eigPv, eigInt;
   void* hpin = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   // phase profiling (opts.profile): events recorded at phase boundaries
@@ -533,6 +533,10 @@ static int prepare_newton(Ctx& C, int n, int m, int prec) {
 static int prepare_eig(Ctx& C, int q) {
   const size_t qq = (size_t)q * q;
   LYAP_TRY(ensure(C.eigWork32, std::max(2 * qq, bjac_work_floats(q)) * 4 + 64));
+  if (eig_big_floats(q) > 0) {
+    LYAP_TRY(ensure(C.eigBig, eig_big_floats(q) * 4 + 64));
+    C.eig.big = P<float>(C.eigBig);
+  }
   LYAP_TRY(ensure(C.eigX, qq * 8 + 64));
   LYAP_TRY(ensure(C.eigR, qq * 8 + 64));
   LYAP_TRY(ensure(C.eigS, qq * 8 + 64));
@@ -1030,7 +1034,7 @@ int lyap_ctx_destroy(lyap_ctx_t* C) {
                 &C->dmu, &C->dex, &C->F, &C->tau, &C->Tm, &C->TP, &C->H, &C->w, &C->Qh, &C->Csel, &C->Lp,
                 &C->Lm, &C->Zs, &C->Zbest, &C->G, &C->gram, &C->ysol, &C->ybest, &C->ytmp, &C->Lw, &C->Sd,
                 &C->Vs, &C->Lst, &C->Rtau, &C->Bm, &C->VB, &C->qrBar, &C->qrStatus, &C->qrCand, &C->qrNorms, &C->qrPiv, &C->qrRdiag, &C->qrWork,
-                &C->qrRank, &C->eigWork32, &C->eigX, &C->eigR, &C->eigS, &C->eigHX, &C->eigE, &C->eigLam,
+                &C->qrRank, &C->eigWork32, &C->eigBig, &C->eigX, &C->eigR, &C->eigS, &C->eigHX, &C->eigE, &C->eigLam,
                 &C->eigRed, &C->eigW, &C->eigPv, &C->eigInt, &C->At, &C->Ct, &C->ZY, &C->adjT, &C->Hf, &C->tl, &C->inv1};
   for (Buf* b : all) free_buf(*b);
   for (lyap_ctx* w : C->pool) lyap_ctx_destroy(w);

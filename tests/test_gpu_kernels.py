@@ -161,10 +161,54 @@ def test_sym_eig_order_beyond_split_grid(refine):
     assert np.linalg.norm(S - np.diag(np.diag(S)), 2) <= tol * nh * (1 if refine else q ** 0.5)
 
 
+@pytest.mark.parametrize("q,refine", [(1500, False), (1500, True), (4096, False), (4096, True), (8192, True)])
+def test_sym_eig_super_block_orders(q, refine):
+    # orders above the block Jacobi's 1280: Jacobi over super-blocks of at most 512 indices
+    # (uneven at 1500: 4 blocks of 375), each pair diagonalised by the block Jacobi, then the
+    # FP64 refinement; checked against LAPACK (eigvalsh) and by the residual and orthogonality
+    g = gen.rng(7000 + q)
+    B = g.standard_normal((q, q))
+    H = (B + B.T) / 2
+    H[0, 0] += 3.0
+    w, Q = lib().sym_eig(T(H), refine)
+    w, Q = N(w), N(Q)
+    nh = np.linalg.norm(H, 2)
+    wref = np.linalg.eigvalsh(H)
+    if refine:
+        tol = 1e-13 * max(1.0, (q / 1024) ** 0.5)
+        assert np.max(np.abs(w - wref)) <= tol * nh
+        assert np.max(np.abs(Q.T @ Q - np.eye(q))) <= tol
+        S = Q.T @ (H @ Q)
+        assert np.linalg.norm(S - np.diag(np.diag(S))) <= tol * nh * q ** 0.5
+    else:
+        assert np.max(np.abs(w - wref)) <= 2e-5 * nh * q ** 0.5
+        assert np.max(np.abs(Q.T @ Q - np.eye(q))) <= 1e-4
+        assert np.linalg.norm(H @ Q - Q * w) <= 2e-5 * nh * q
+    assert np.all(np.diff(w) >= 0.0)
+
+
+def test_sym_eig_super_block_low_rank_graded():
+    # q = 2048 with eigenvalues 1 .. 1e-16 and a 600-fold zero eigenvalue (the spectrum shape
+    # of the projected-update cores of nearly full-rank solutions): FP64-accurate pairs
+    q = 2048
+    g = gen.rng(7100)
+    Qm, _ = np.linalg.qr(g.standard_normal((q, q)))
+    lam = np.concatenate([10.0 ** (-16.0 * np.arange(q - 600) / (q - 600)), np.zeros(600)])
+    H = (Qm * lam) @ Qm.T
+    H = (H + H.T) / 2
+    w, Q = lib().sym_eig(T(H), True)
+    w, Q = N(w), N(Q)
+    nh = np.linalg.norm(H, 2)
+    assert np.max(np.abs(w - np.linalg.eigvalsh(H))) <= 2e-13 * nh
+    assert np.max(np.abs(Q.T @ Q - np.eye(q))) <= 2e-13
+    S = Q.T @ H @ Q
+    assert np.linalg.norm(S - np.diag(np.diag(S)), 2) <= 2e-13 * nh
+
+
 # ------------------------------------------------ FP64 products on the tensor cores
 
 @pytest.mark.parametrize("m,n,k", [(1, 1, 1), (5, 7, 3), (128, 64, 64), (300, 200, 1100), (1000, 421, 1024),
-                                   (130, 129, 2050)])
+                                   (130, 129, 2050), (64, 40, 20000)])
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
 def test_dgemm_tensor_emulation_fp64_accuracy(m, n, k, ta, tb):
     # lyap_dgemm method 2 (FP16 digit slices on tcgen05, FP64 sums) against the exact product's
@@ -195,6 +239,22 @@ def test_dgemm_tensor_matches_simt_and_exact_integers():
     for method in ("tensor", "simt", "auto"):
         C = N(lib().dgemm(T(A), T(B), method=method))
         assert np.array_equal(C, ref), method
+
+
+def test_dgemm_tensor_split_k_exact_and_deterministic():
+    # few output tiles and a long K: the product is split over K and the partial products summed
+    # in a fixed order; integer data keeps every partial sum exact, and repeated calls agree bitwise
+    g = gen.rng(3200)
+    for (m, n, k) in ((100, 30, 5000), (260, 33, 3000), (40, 300, 2300)):
+        A = g.integers(-1000, 1000, size=(m, k)).astype(np.float64)
+        B = g.integers(-1000, 1000, size=(k, n)).astype(np.float64)
+        ref = A @ B
+        C1 = N(lib().dgemm(T(A), T(B), method="tensor"))
+        assert np.array_equal(C1, ref), (m, n, k)
+        Ar, Br = g.standard_normal((m, k)), g.standard_normal((k, n))
+        R1 = N(lib().dgemm(T(Ar), T(Br), method="tensor"))
+        R2 = N(lib().dgemm(T(Ar), T(Br), method="tensor"))
+        assert np.array_equal(R1, R2)
 
 
 def test_dgemm_zero_and_empty():

@@ -300,3 +300,20 @@ def test_ir_stagnation_rule_on_gpu():
     assert _stagnation_stop(oinfo.res_hist) == len(oinfo.res_hist) - 1
     assert oinfo.res_final <= 1e-14
     assert info.res_final <= 10.0 * oinfo.res_final, (info.res_final, oinfo.res_final)
+
+
+def test_ir_ldlt_indefinite_n4096_fp32():
+    # the LDL^T family at full size (n = 4096, indefinite S, normal blocks, p = 1), FP32 inner
+    # solves: the projected-update eigenproblems reach order ~4096 (Jacobi over super-blocks);
+    # the result against the Schur-block closed form and the oracle's Eq. (4.1)
+    from tests.test_oracle_pins import schur_blocks_solution
+    d = gen.normal_blocks(n=4096, p=1, m=8, indefinite=True)
+    A, L, S = d["A"], d["L"], d["S"]
+    W = L @ S @ L.T
+    Z, D, info = lib().solve_ir(T(A), T(L), S=T(S), u_s="fp32", tau_ir=1e-12, imax=20)
+    assert info.converged, info.as_dict()
+    X = schur_blocks_solution(d["Q"], d["alpha"], d["beta"], W)
+    Zn, Dn = N(Z), N(D)
+    assert rel((Zn * Dn) @ Zn.T, X) <= 1e-10
+    assert O.residual_eq41(A, Zn, W, Dn) <= 1e-12
+    assert abs(info.res_final - O.residual_eq41(A, Zn, W, Dn)) <= 1e-3 * info.res_final
