@@ -437,9 +437,10 @@ def run_case(args):
     sweep3:<n>          LDL^T condition sweep (A = Q T Q^T normal 2 x 2 blocks, p = 1..4, W = L S L^T
                         indefinite, m = 8): attainable residual and time for FP16, BF16, FP32 inner
                         solves and the FP64 sign-Newton solve (one JSON line per run)
-    adjoint:<n>[:<k>]   forward FP16-inner IR + lyap_adjoint of l = trace(C X C^T) (p = 2 family,
-                        m = 4, C 4 x n): times, and central differences of the forward solver on
-                        k (default 20) random directions of A and L (relative errors)
+    adjoint:<n>[:<k>[:<u>]]  forward IR (inner precision u, default fp32; checkpoints every 4
+                        Newton steps) + lyap_adjoint of l = trace(C X C^T) (p = 2 family, m = 4,
+                        C 4 x n): times, and central differences of FP64 sign-Newton losses on k
+                        (default 20) random directions of A and L (relative errors)
     config1             FP64 sign-Newton on the 8 x 8-grid Laplacian (n = 64, determinantal scaling,
                         Frobenius stop 1e-12 n): microseconds per solve (CUDA events)"""
     import numpy as np
@@ -624,14 +625,16 @@ def run_case(args):
         import time
         import lyapgen
         n = int(rest[0]) if rest else 1024
+        u_fwd = rest[2] if len(rest) > 2 else "fp32"
         d = lyapgen.normal_blocks(n=n, p=2, m=4, indefinite=False)
         Cm = lyapgen.loss_weights(4, n)
         A, L, C = torch.tensor(d["A"], device=dev), torch.tensor(d["L"], device=dev), torch.tensor(Cm, device=dev)
-        o = lyap.make_opts(u_s="fp16", tau_ir=1e-13, imax=30)
-        o64 = lyap.make_opts(u_s="fp64", tau_ir=1e-15, imax=10)  # the finite differences in FP64
+        o = lyap.make_opts(u_s=u_fwd, tau_ir=1e-12, imax=30, ckpt_every=4)
+        o64 = lyap.make_opts(u_s="fp64")  # the finite differences: FP64 sign-Newton losses
 
         def loss(Aa, Ll, opts):
-            Z, _, inf = lyap.solve_ir(Aa, Ll, opts=opts)
+            fn = lyap.sign_solve if opts is o64 else lyap.solve_ir
+            Z, _, inf = fn(Aa, Ll, opts=opts)
             CZ = C @ Z
             return float((CZ * CZ).sum()), Z, inf
 
@@ -663,11 +666,12 @@ def run_case(args):
             rel_L.append(abs(fd - an) / abs(an))
             nrm_L.append(abs(fd - an) / (gL * float(F.norm())))
         mx = lambda v: max(v) if v else None  # noqa: E731
-        print(json.dumps({"case": "adjoint", "n": n, "u_s": "fp16", "forward_res": inf.res_final,
+        print(json.dumps({"case": "adjoint", "n": n, "u_s": u_fwd, "ckpt_every": 4, "forward_res": inf.res_final,
+                          "forward_converged": bool(inf.converged), "forward_ir_steps": inf.ir_steps,
                           "forward_rank": inf.rank, "adjoint_res": out["info"].res_final,
                           "adjoint_inversions": out["info"].n_inversions,
                           "forward_seconds": t_fwd, "adjoint_seconds": t_adj, "fd_directions": dirs, "fd_step": h,
-                          "fd_precision": "fp64 refinement, tau 1e-15",
+                          "fd_precision": "fp64 sign-Newton losses",
                           "max_rel_err_dA": mx(rel_A), "max_rel_err_dL": mx(rel_L),
                           "max_err_dA_over_grad_norm": mx(nrm_A), "max_err_dL_over_grad_norm": mx(nrm_L)}))
         return 0

@@ -187,3 +187,50 @@ def test_adjoint_checkpointed_equals_stored(n):
         ref = O.adjoint(d["A"], d["L"], N(Cm))
         assert relF(grads[1][0], ref["dA"]) <= 1e-9
         assert relF(grads[1][1], ref["dL"]) <= 1e-9
+
+
+def test_adjoint_n2048_normal_blocks_checkpointed_and_central_differences():
+    # the differentiable solve at full size: n = 2048 normal blocks (p = 2, kappa ~ 1e4),
+    # W = L L^T (L n x 4), l = trace(C X C^T) with C 4 x n.  The forward refinement uses FP32
+    # inner solves (FP16 and BF16 are past their kappa range here: u_s kappa > 1; they stall
+    # near 1e-11 and 6e-5).  Adjoint from checkpoints every 4 Newton steps equals the one from
+    # the stored inverses; both against central differences (step 1e-6) of FP64 sign-Newton
+    # losses on 4 random directions of A and of L.
+    lp = lib()
+    d = gen.normal_blocks(n=2048, p=2, m=4, indefinite=False)
+    Cm = gen.loss_weights(4, 2048)
+    A, L, C = T(d["A"]), T(d["L"]), T(Cm)
+    grads = []
+    for ck in (0, 4):
+        o = lp.make_opts(u_s="fp32", tau_ir=1e-12, imax=20, ckpt_every=ck)
+        Z, _, info = lp.solve_ir(A, L, opts=o)
+        assert info.converged, info.as_dict()
+        out = lp.adjoint(A, L, Z, C, opts=o)
+        assert out["info"].converged, out["info"].as_dict()
+        if ck:
+            assert out["info"].n_inversions > 0
+        grads.append((N(out["dA"]), N(out["dL"])))
+    assert relF(grads[1][0], grads[0][0]) <= 1e-12
+    assert relF(grads[1][1], grads[0][1]) <= 1e-12
+    dA, dL = grads[1]
+    o64 = lp.make_opts(u_s="fp64")
+
+    def loss(Aa, Ll):
+        Zz, _, inf = lp.sign_solve(Aa, Ll, opts=o64)
+        assert inf.res_final <= 1e-14
+        CZ = C @ Zz
+        return float((CZ * CZ).sum())
+
+    g = gen.rng(gen.SEED_BASE + 49)
+    h = 1e-6
+    for k in range(4):
+        E = g.standard_normal((2048, 2048))
+        E *= float(A.norm()) / np.linalg.norm(E)
+        fd = (loss(A + h * T(E), L) - loss(A - h * T(E), L)) / (2 * h)
+        an = float(np.sum(dA * E))
+        assert abs(fd - an) <= 1e-6 * abs(an), (k, fd, an)
+        F = g.standard_normal((2048, 4))
+        F *= float(L.norm()) / np.linalg.norm(F)
+        fd = (loss(A, L + h * T(F)) - loss(A, L - h * T(F))) / (2 * h)
+        an = float(np.sum(dL * F))
+        assert abs(fd - an) <= 1e-6 * abs(an), (k, fd, an)
