@@ -65,7 +65,8 @@ def rnd(x, prec: str):
 class Opts:
     """Algorithm parameters; defaults are the paper's (Sec. 4.1)."""
     u_s: str = "fp64"              # solver precision (Algorithms IR-Chol / IR-LDLT)
-    scaling: str = "frob"          # "frob" (Sec. 4, chosen), "det", "none"   (Sec. 3)
+    scaling: str = "frob"          # "frob" (Sec. 4, chosen), "det", "norm2", "spectral", "none"
+                                   # (the scalings listed in Sec. 3.1)
     tau_newton: float = 0.0        # <= 0: 10 sqrt(n u_s)  (Eq. (3.4))
     newton_norm: str = "one"       # "one": ||A_k + I||_1 (Eq. (3.4)); "fro": ||A_k + I||_F
     stop_after: int = 2            # "two more iterations" (Sec. 3.2): the iteration ends at the
@@ -217,9 +218,11 @@ def newton_sequence(A: np.ndarray, opts: Opts) -> NewtonRecord:
     """The matrix part of the scaled sign-function Newton iteration, Eq. (3.1a).
 
     A_k = (mu_{k-1} A_{k-1} + mu_{k-1}^{-1} A_{k-1}^{-1}) / 2 with
-      Frobenius scaling mu = (||A^{-1}||_F / ||A||_F)^{1/2}, or
+      Frobenius scaling mu = (||A^{-1}||_F / ||A||_F)^{1/2},
       determinantal scaling mu = |det A|^{-1/n} (evaluated from the LU diagonal in
-      logarithms, since the determinant itself over/underflows, Sec. 4).
+      logarithms, since the determinant itself over/underflows, Sec. 4),
+      2-norm scaling mu = (||A^{-1}||_2 / ||A||_2)^{1/2}, or
+      spectral scaling mu = (rho(A^{-1}) / rho(A))^{1/2} (rho: spectral radius); Sec. 3.1.
     Scaling is switched off for good once delta_k = ||A_k - A_{k-1}||_F / ||A_k||_F < 1e-2.
     The stop test is ||A_k + I|| <= tau_N (Eq. (3.4)) or, once scaling is off,
     delta_k > delta_{k-1}/2 (Sec. 4); the iteration ends at the second iterate counted
@@ -243,6 +246,10 @@ def newton_sequence(A: np.ndarray, opts: Opts) -> NewtonRecord:
         elif scaling_on and opts.scaling == "det":
             lu, _, _ = getrf_pp(Ak)
             mu = math.exp(-np.sum(np.log(np.abs(np.diag(lu)))) / n)
+        elif scaling_on and opts.scaling == "norm2":
+            mu = math.sqrt(np.linalg.norm(Xk, 2) / np.linalg.norm(Ak, 2))
+        elif scaling_on and opts.scaling == "spectral":
+            mu = math.sqrt(np.max(np.abs(np.linalg.eigvals(Xk))) / np.max(np.abs(np.linalg.eigvals(Ak))))
         else:
             mu = 1.0
         Anew = rnd(0.5 * (mu * Ak + Xk / mu), p)

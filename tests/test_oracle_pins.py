@@ -171,6 +171,46 @@ def test_sign_newton_scaling_invariance():
     assert abs(r2.mus[0] * 8.0 - r1.mus[0]) < 1e-12 * r1.mus[0]
 
 
+def test_sign_newton_norm2_and_spectral_scaling_closed_forms():
+    # Sec. 3.1 scalings on matrices with known norms and spectra.
+    # (1) Upper triangular A = [[-1, 10, 0], [0, -2, 5], [0, 0, -4]]: rho(A) = 4 and
+    # rho(A^{-1}) = 1, so the spectral mu_0 = 1/2 exactly.  The squared singular values are
+    # the roots of x^3 - t x^2 + c x - det(A)^2 with t = ||A||_F^2 = 146 and
+    # c = (t^2 - tr((A^T A)^2)) / 2 (integers); sigma_max(A^{-1}) = 1 / sigma_min(A), so the
+    # 2-norm mu_0 = (x_min x_max)^(-1/4).  Frobenius: ||A^{-1}||_F^2 = 65.765625 by hand.
+    A = np.array([[-1.0, 10.0, 0.0], [0.0, -2.0, 5.0], [0.0, 0.0, -4.0]])
+    M = A.T @ A
+    t = float(np.trace(M))
+    c = (t * t - float(np.trace(M @ M))) / 2
+    x = np.sort(np.roots([1.0, -t, c, -64.0]).real)
+    mu_n2 = (x[0] * x[2]) ** -0.25
+    mu_fro = math.sqrt(math.sqrt(65.765625) / math.sqrt(146.0))
+    r_sp = O.newton_sequence(A, O.Opts(u_s="fp64", scaling="spectral"))
+    r_n2 = O.newton_sequence(A, O.Opts(u_s="fp64", scaling="norm2"))
+    r_fr = O.newton_sequence(A, O.Opts(u_s="fp64", scaling="frob"))
+    assert abs(r_sp.mus[0] - 0.5) <= 1e-15
+    assert abs(r_n2.mus[0] - mu_n2) <= 1e-12 * mu_n2
+    assert abs(r_fr.mus[0] - mu_fro) <= 1e-14 * mu_fro
+    assert min(abs(mu_n2 - mu_fro), abs(mu_n2 - 0.5), abs(mu_fro - 0.5)) > 1e-2
+    for r in (r_sp, r_n2, r_fr):
+        assert np.linalg.norm(r.A_final + np.eye(3)) <= 1e-12
+    # (2) symmetric negative definite A with spectrum in [-b, -a]: both scalings give
+    # mu_0 = 1 / sqrt(a b), which maps the two extreme eigenvalues to the same value of
+    # A_1 = (mu A + (mu A)^{-1}) / 2: -(sqrt(b/a) + sqrt(a/b)) / 2
+    g = gen.rng(77)
+    Q, _ = np.linalg.qr(g.standard_normal((12, 12)))
+    lam = -np.geomspace(0.5, 200.0, 12)
+    S = (Q * lam) @ Q.T
+    S = (S + S.T) / 2
+    for sc in ("norm2", "spectral"):
+        r = O.newton_sequence(S, O.Opts(u_s="fp64", scaling=sc))
+        assert abs(r.mus[0] - 1.0 / math.sqrt(0.5 * 200.0)) <= 1e-13 / math.sqrt(100.0)
+        A1 = 0.5 * (r.mus[0] * S + np.linalg.inv(S) / r.mus[0])
+        e = np.linalg.eigvalsh(A1)
+        assert abs(e[0] - (-(math.sqrt(400.0) + math.sqrt(1 / 400.0)) / 2)) <= 1e-12 * abs(e[0])
+        assert np.linalg.norm(r.A_final + np.eye(12)) <= 1e-10
+
+
 def test_newton_chol_fp64_laplacian_config():
     d = gen.fp64_laplacian(8, 2)
     A, L = d["A"], d["L"]
