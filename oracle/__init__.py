@@ -23,6 +23,11 @@ Functions and the passages they follow:
 * ``residual_eq41``        -- relative residual of Eq. (4.1), explicit n x n formation
 * ``adjoint``              -- gradient of trace(C X C^T) (not in the paper; derived from Eq. (1.1))
 * ``getrf_pp``             -- LU with partial pivoting (the factorisation behind the inversions)
+* ``newton_sequence``      -- the scaled Newton iteration with the scalings of Sec. 3.1
+  (Frobenius, determinantal, 2-norm, spectral)
+* ``sign_block``/``sign_matrix``/``frechet_sign``/``kappa_sign_fro`` -- sign(B) of
+  B = [[A, W], [0, -A^T]], its Frechet derivative and kappa_sign(B) in the Frobenius norm,
+  the indicator Sec. 4.2 uses to explain the accuracy of the Newton solver
 
 Pins (tests/test_oracle_*.py) tie every function to something other than itself:
 the Kronecker form Eq. (2.1) solved densely, closed forms for diagonal and

@@ -16,6 +16,7 @@ __all__ = [
     "UNIT", "Opts", "rnd", "bartels_stewart", "getrf_pp", "rank_trunc_chol", "rank_trunc_ldlt",
     "newton_sequence", "NewtonRecord", "IRInfo", "newton_chol", "newton_ldlt", "res_fac_chol", "sol_upt_chol", "res_fac_ldlt", "sol_upt_ldlt",
     "ir_chol", "ir_ldlt", "residual_eq41", "adjoint", "norm_xyx", "lyap_operator_kappa2_normal",
+    "sign_block", "sign_matrix", "frechet_sign", "kappa_sign_fro",
 ]
 
 # Unit roundoffs of Table 1.1 (t significand bits incl. the implicit bit: u = 2^-t).
@@ -576,3 +577,47 @@ def adjoint(A, L, C, S=None):
     Y = bartels_stewart(A.T, G)
     return {"X": X, "Y": Y, "loss": float(np.trace(C @ X @ C.T)),
             "dA": 2.0 * Y @ X, "dL": 2.0 * Y @ L @ S, "dS": L.T @ Y @ L}
+
+
+# ---------------------------------------------------------------------------------------
+# Condition of the matrix sign function at B = [[A, W], [0, -A^T]] (Sec. 4.2: the sign-
+# Newton iteration for Eq. (1.1) computes sign(B); kappa_sign(B) in the Frobenius norm
+# predicts its accuracy).  Plain definitions for small orders: the eigendecomposition
+# B = V diag(lambda) V^{-1} (B diagonalisable, no eigenvalue on the imaginary axis).
+# ---------------------------------------------------------------------------------------
+def sign_block(A: np.ndarray, W: np.ndarray) -> np.ndarray:
+    """B = [[A, W], [0, -A^T]], whose sign is [[-I, 2X], [0, I]] for Hurwitz A (Sec. 3)."""
+    n = A.shape[0]
+    return np.block([[A, W], [np.zeros((n, n)), -A.T]])
+
+
+def sign_matrix(B: np.ndarray) -> np.ndarray:
+    """sign(B) = V diag(sign(Re lambda_i)) V^{-1}."""
+    lam, V = np.linalg.eig(B)
+    return np.real(V @ np.diag(np.sign(lam.real)) @ np.linalg.inv(V))
+
+
+def frechet_sign(B: np.ndarray, E: np.ndarray) -> np.ndarray:
+    """Frechet derivative L_sign(B, E) = V (D o (V^{-1} E V)) V^{-1} with the divided
+    differences D_ij = (sign lambda_i - sign lambda_j) / (lambda_i - lambda_j), 0 where the
+    signs agree (the derivative of a function constant on each half plane)."""
+    lam, V = np.linalg.eig(B)
+    sg = np.sign(lam.real)
+    Vi = np.linalg.inv(V)
+    dl = lam[:, None] - lam[None, :]
+    same = sg[:, None] == sg[None, :]
+    D = np.where(same, 0.0, (sg[:, None] - sg[None, :]) / np.where(same, 1.0, dl))
+    return np.real(V @ (D * (Vi @ E @ V)) @ Vi)
+
+
+def kappa_sign_fro(B: np.ndarray) -> float:
+    """kappa_sign(B) = ||L_sign(B)||_F ||B||_F / ||sign(B)||_F, where ||L||_F is the 2-norm of
+    the N^2 x N^2 matrix of E -> L_sign(B, E) in vec form (columns L(B, e_i e_j^T))."""
+    N = B.shape[0]
+    K = np.empty((N * N, N * N))
+    for j in range(N):
+        for i in range(N):
+            E = np.zeros((N, N))
+            E[i, j] = 1.0
+            K[:, i + j * N] = frechet_sign(B, E).reshape(-1, order="F")
+    return float(np.linalg.norm(K, 2) * np.linalg.norm(B, "fro") / np.linalg.norm(sign_matrix(B), "fro"))

@@ -500,3 +500,40 @@ def test_adjoint_diagonal_closed_form():
     out = O.adjoint(np.diag(a), L, C)
     G = C.T @ C
     assert rel(out["Y"], -G / (a[:, None] + a[None, :])) < 1e-12
+
+
+
+# ----------------------------------------------------- condition of the sign function
+
+def test_kappa_sign_diagonal_closed_form():
+    # diagonal B: L_sign(B, E)_ij = E_ij (sign d_i - sign d_j) / (d_i - d_j), so
+    # ||L|| = 2 / (smallest positive d - largest negative d) and ||sign B||_F = sqrt(N)
+    d = np.array([-3.0, -0.5, 0.25, 2.0, -7.0, 1.5])
+    B = np.diag(d)
+    k = O.kappa_sign_fro(B)
+    ref = 2.0 / (0.25 - (-0.5)) * np.linalg.norm(d) / math.sqrt(6.0)
+    assert abs(k - ref) <= 1e-12 * ref
+
+
+def test_frechet_sign_against_library_sign_central_differences():
+    # L_sign(B, E) against central differences of scipy's sign function (an independent route)
+    g = gen.rng(88)
+    B = g.standard_normal((5, 5)) + np.diag([3.0, -3.0, 2.5, -2.0, 4.0])
+    E = g.standard_normal((5, 5))
+    assert np.linalg.norm(O.sign_matrix(B) - sla.signm(B)) <= 1e-10
+    h = 1e-6
+    fd = (sla.signm(B + h * E) - sla.signm(B - h * E)) / (2 * h)
+    assert np.linalg.norm(O.frechet_sign(B, E) - fd) <= 1e-6 * np.linalg.norm(fd)
+
+
+def test_sign_block_structure_is_lyapunov_solution():
+    # sign([[A, W], [0, -A^T]]) = [[-I, 2X], [0, I]] with A X + X A^T + W = 0 (Hurwitz A)
+    d = gen.convdiff_shifted(grid=4, m=2)
+    A, L = d["A"], d["L"]
+    W = L @ L.T
+    S = O.sign_matrix(O.sign_block(A, W))
+    n = A.shape[0]
+    X = O.bartels_stewart(A, W)
+    assert np.linalg.norm(S[:n, :n] + np.eye(n)) <= 1e-9
+    assert np.linalg.norm(S[n:, n:] - np.eye(n)) <= 1e-9
+    assert np.linalg.norm(S[:n, n:] - 2 * X) <= 1e-9 * np.linalg.norm(X)
