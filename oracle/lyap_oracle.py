@@ -17,6 +17,7 @@ __all__ = [
     "newton_sequence", "NewtonRecord", "IRInfo", "newton_chol", "newton_ldlt", "res_fac_chol", "sol_upt_chol", "res_fac_ldlt", "sol_upt_ldlt",
     "ir_chol", "ir_ldlt", "residual_eq41", "adjoint", "norm_xyx", "lyap_operator_kappa2_normal",
     "sign_block", "sign_matrix", "frechet_sign", "kappa_sign_fro",
+    "ADIRecord", "adi_shifts", "adi_record", "lr_adi_chol", "lr_adi_ldlt",
 ]
 
 # Unit roundoffs of Table 1.1 (t significand bits incl. the implicit bit: u = 2^-t).
@@ -86,6 +87,11 @@ class Opts:
     stag_theta: float = 0.9        # Eq. (4.2)
     stag_count: int = 2
     project_psd: bool = True       # SolUpt projection onto the PSD cone (Sec. 2.1)
+    inner: str = "sign"            # inner solver: "sign" (Sec. 3) or "adi" (low-rank ADI, the
+                                   # alternative Sec. 5 names; real shifts, see lr_adi_*)
+    adi_shifts: int = 8            # number of cyclic real shifts
+    adi_tol: float = 0.0           # <= 0: max(10 u_s, 1e-14); ||W S W^T||_F <= tol ||L S L^T||_F
+    adi_maxit: int = 200
 
 
 def _u(prec: str) -> float:
@@ -326,6 +332,90 @@ def newton_ldlt(A: np.ndarray, L: np.ndarray, y: np.ndarray, opts: Opts,
 
 
 # ---------------------------------------------------------------------------
+# Low-rank ADI as the inner solver (Sec. 5 names ADI-based solvers as an alternative inside
+# the same refinement framework; the iteration is the standard real-shift low-rank ADI)
+# ---------------------------------------------------------------------------
+@dataclass
+class ADIRecord:
+    """Shifts and the shifted inverses (A + p_j I)^{-1} rounded to u_s (depend on A only, so
+    every correction solve reuses them, as the sign-Newton sequence of Sec. 3.4)."""
+    shifts: list = field(default_factory=list)
+    inverses: list = field(default_factory=list)
+
+
+def adi_shifts(a: float, b: float, count: int) -> np.ndarray:
+    """Real shifts for a spectrum with |lambda| in [a, b]: the geometric grid
+    p_j = -b (a / b)^((2j - 1) / (2 count)), j = 1..count."""
+    j = np.arange(1, count + 1)
+    return -b * (a / b) ** ((2 * j - 1) / (2.0 * count))
+
+
+def adi_record(A: np.ndarray, opts: Opts) -> ADIRecord:
+    """Shifts from the 2-norm bounds a = 1 / ||A^{-1}||_2, b = ||A||_2 and the inverses."""
+    n = A.shape[0]
+    a = 1.0 / np.linalg.norm(np.linalg.inv(A), 2)
+    b = np.linalg.norm(A, 2)
+    rec = ADIRecord()
+    for p in adi_shifts(a, b, opts.adi_shifts):
+        rec.shifts.append(float(p))
+        rec.inverses.append(rnd(np.linalg.inv(rnd(A + p * np.eye(n), opts.u_s)), opts.u_s))
+    return rec
+
+
+def _lr_adi(A, L, y, opts: Opts, rec: ADIRecord | None, ldlt: bool):
+    """V_j = (A + p_j I)^{-1} W_{j-1}, W_j = W_{j-1} - 2 p_j V_j (W_0 = L, shifts cyclic);
+    Cholesky type: Z_j = [Z_{j-1}, sqrt(-2 p_j) V_j]; LDL^T type: Z_j = [Z_{j-1}, V_j] with
+    weights -2 p_j y.  Then A X_j + X_j A^T + L diag(y) L^T = W_j diag(y) W_j^T for
+    X_j = Z_j diag(D_j) Z_j^T; the iteration stops once ||W diag(y) W^T||_F <= adi_tol
+    ||L diag(y) L^T||_F.  Every matrix result is rounded to u_s; Z is truncated by
+    RankTruncChol / RankTruncLdlt whenever cols(Z) > rho n, as in the Newton solver."""
+    n = A.shape[0]
+    p_ = opts.u_s
+    if rec is None:
+        rec = adi_record(A, opts)
+    tol = opts.adi_tol if opts.adi_tol > 0 else max(10.0 * _u(p_), 1e-14)
+    rtol = opts.rank_tol if opts.rank_tol > 0 else (_u(p_) if ldlt else math.sqrt(_u(p_)))
+    y0 = np.ones(L.shape[1]) if y is None else np.asarray(y, dtype=np.float64)
+    W = rnd(L, p_)
+    nrm0 = np.linalg.norm((W * y0) @ W.T, "fro")
+    Z = np.zeros((n, 0))
+    yZ = np.zeros(0)
+    steps = 0
+    for it in range(opts.adi_maxit):
+        if nrm0 == 0.0 or np.linalg.norm((W * y0) @ W.T, "fro") <= tol * nrm0:
+            break
+        j = it % len(rec.shifts)
+        pj = rec.shifts[j]
+        V = rnd(rec.inverses[j] @ W, p_)
+        W = rnd(W - 2.0 * pj * V, p_)
+        if ldlt:
+            Z = np.hstack([Z, V])
+            yZ = np.concatenate([yZ, -2.0 * pj * y0])
+        else:
+            Z = rnd(np.hstack([Z, math.sqrt(-2.0 * pj) * V]), p_)
+        steps += 1
+        if Z.shape[1] > opts.rho * n:
+            if ldlt:
+                Z, yZ = rank_trunc_ldlt(Z, yZ, rtol)
+                Z = rnd(Z, p_)
+            else:
+                Z = rnd(rank_trunc_chol(Z, rtol), p_)
+    return Z, yZ, W, rec, steps
+
+
+def lr_adi_chol(A, L, opts: Opts, rec: ADIRecord | None = None):
+    """Low-rank ADI for A X + X A^T + L L^T = 0: returns (Z, rec, W, steps), X ~ Z Z^T."""
+    Z, _, W, rec, steps = _lr_adi(A, L, None, opts, rec, False)
+    return Z, rec, W, steps
+
+
+def lr_adi_ldlt(A, L, y, opts: Opts, rec: ADIRecord | None = None):
+    """Low-rank ADI for A X + X A^T + L diag(y) L^T = 0: returns (Z, yZ, rec, W, steps)."""
+    Z, yZ, W, rec, steps = _lr_adi(A, L, y, opts, rec, True)
+    return Z, yZ, rec, W, steps
+
+
+# ---------------------------------------------------------------------------
 # Residual factorisation and solution update, Sec. 2
 # ---------------------------------------------------------------------------
 
@@ -444,7 +534,8 @@ class IRInfo:
 
 
 def ir_chol(A, L, opts: Opts):
-    """Algorithm IR-Chol (Sec. 2.1) with the sign-Newton solver (Sec. 3) and Sec. 4.1 rules.
+    """Algorithm IR-Chol (Sec. 2.1) with the sign-Newton solver (Sec. 3; or low-rank ADI,
+    ``opts.inner``) and Sec. 4.1 rules.
 
     The inverse sequence of the first solve is stored and replayed by every
     correction solve (Sec. 3.4): the sequence depends on A only.
@@ -454,7 +545,13 @@ def ir_chol(A, L, opts: Opts):
     tau_ir = opts.tau_ir if opts.tau_ir > 0 else n * UNIT["fp64"]
     eta_s = opts.eta_s if opts.eta_s > 0 else 10.0 * UNIT["fp64"]
     info = IRInfo()
-    Z, rec = newton_chol(A, L, opts)
+    if opts.inner == "adi":
+        def solve(Lr, r):
+            return lr_adi_chol(A, Lr, opts, r)[:2]
+    else:
+        def solve(Lr, r):
+            return newton_chol(A, Lr, opts, r)
+    Z, rec = solve(L, None)
     K = len(rec.inverses)
     info.n_inversions = K
     info.newton_calls, info.newton_total, info.newton_max = 1, K, K
@@ -483,8 +580,8 @@ def ir_chol(A, L, opts: Opts):
         if i == opts.imax + 1:
             break
         Lp, Lm = rnd(Lp, opts.u_s), rnd(Lm, opts.u_s)
-        Zp = newton_chol(A, Lp, opts, rec)[0] if Lp.shape[1] else np.zeros((n, 0))
-        Zm = newton_chol(A, Lm, opts, rec)[0] if Lm.shape[1] else np.zeros((n, 0))
+        Zp = solve(Lp, rec)[0] if Lp.shape[1] else np.zeros((n, 0))
+        Zm = solve(Lm, rec)[0] if Lm.shape[1] else np.zeros((n, 0))
         info.newton_calls += 1
         info.newton_total += K
         Z = sol_upt_chol(Z, Zp, Zm, eta_s)
@@ -495,7 +592,8 @@ def ir_chol(A, L, opts: Opts):
 
 
 def ir_ldlt(A, L, S, opts: Opts):
-    """Algorithm IR-LDLT (Sec. 2.3) with the sign-Newton solver (Sec. 3) and Sec. 4.1 rules.
+    """Algorithm IR-LDLT (Sec. 2.3) with the sign-Newton solver (Sec. 3; or low-rank ADI,
+    ``opts.inner``) and Sec. 4.1 rules.
 
     S is diagonalised at entry (S = V diag(s) V^T, L <- L V), which is exact, so that
     every inner factor Y is a diagonal vector.  When S is indefinite the PSD
@@ -510,7 +608,14 @@ def ir_ldlt(A, L, S, opts: Opts):
     tau_ir = opts.tau_ir if opts.tau_ir > 0 else n * UNIT["fp64"]
     eta_s = opts.eta_s if opts.eta_s > 0 else 10.0 * UNIT["fp64"]
     info = IRInfo()
-    Z, y, rec = newton_ldlt(A, L, s, opts)
+    if opts.inner == "adi":
+        def solve(Lr, yr, r):
+            Zr, yZ, r2, _, _ = lr_adi_ldlt(A, Lr, yr, opts, r)
+            return Zr, yZ, r2
+    else:
+        def solve(Lr, yr, r):
+            return newton_ldlt(A, Lr, yr, opts, r)
+    Z, y, rec = solve(L, s, None)
     K = len(rec.inverses)
     info.n_inversions = K
     info.newton_calls, info.newton_total, info.newton_max = 1, K, K
@@ -539,7 +644,7 @@ def ir_ldlt(A, L, S, opts: Opts):
         if i == opts.imax + 1:
             break
         Ld, sd = rnd(Ld, opts.u_s), rnd(sd, opts.u_s)
-        Zd, yd, _ = newton_ldlt(A, Ld, sd, opts, rec)
+        Zd, yd, _ = solve(Ld, sd, rec)
         info.newton_calls += 1
         info.newton_total += K
         Z, y = sol_upt_ldlt(Z, y, Zd, yd, eta_s, project)

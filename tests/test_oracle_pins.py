@@ -537,3 +537,46 @@ def test_sign_block_structure_is_lyapunov_solution():
     assert np.linalg.norm(S[:n, :n] + np.eye(n)) <= 1e-9
     assert np.linalg.norm(S[n:, n:] - np.eye(n)) <= 1e-9
     assert np.linalg.norm(S[:n, n:] - 2 * X) <= 1e-9 * np.linalg.norm(X)
+
+
+
+# ----------------------------------------------------------- low-rank ADI (inner solver)
+
+def test_lr_adi_diagonal_closed_form():
+    # diagonal A = diag(a): after j steps with shifts p_1..p_j, X - X_j = X o (r r^T) with
+    # r_i = prod_k (a_i - p_k) / (a_i + p_k) (the ADI error is R X R^T, R = diag(r))
+    a = -np.array([0.3, 1.0, 2.5, 7.0, 20.0])
+    L = gen.rng(91).standard_normal((5, 2))
+    W = L @ L.T
+    X = -W / (a[:, None] + a[None, :])
+    opts = O.Opts(u_s="fp64", adi_shifts=3, adi_tol=1e-300, adi_maxit=5, rho=10.0)
+    rec = O.ADIRecord(shifts=[-0.5, -2.0, -10.0],
+                      inverses=[np.diag(1.0 / (a + p)) for p in (-0.5, -2.0, -10.0)])
+    Z, _, Wres, steps = O.lr_adi_chol(np.diag(a), L, opts, rec)
+    assert steps == 5
+    r = np.ones(5)
+    for p in [-0.5, -2.0, -10.0, -0.5, -2.0]:
+        r *= (a - p) / (a + p)
+    assert np.linalg.norm(Z @ Z.T - X * (1 - np.outer(r, r))) <= 1e-13 * np.linalg.norm(X)
+    assert np.linalg.norm(Wres @ Wres.T - W * np.outer(r, r)) <= 1e-13 * np.linalg.norm(W)
+
+
+def test_lr_adi_residual_identity_and_ir():
+    # A X_j + X_j A^T + L S L^T = W_j S W_j^T for a nonsymmetric A (both forms), and the
+    # refinement with ADI inner solves reaches the Bartels-Stewart solution
+    d = gen.convdiff_shifted(grid=6, m=2)
+    A, L = d["A"], d["L"]
+    opts = O.Opts(u_s="fp64", adi_maxit=6, adi_tol=1e-300, rho=10.0)
+    Z, rec, Wr, _ = O.lr_adi_chol(A, L, opts)
+    Xj = Z @ Z.T
+    R = A @ Xj + Xj @ A.T + L @ L.T
+    assert np.linalg.norm(R - Wr @ Wr.T) <= 1e-10 * np.linalg.norm(L @ L.T)
+    s = np.array([1.0, -1.0])
+    Zl, yl, _, Wl, _ = O.lr_adi_ldlt(A, L, s, opts, rec)
+    Xl = (Zl * yl) @ Zl.T
+    Rl = A @ Xl + Xl @ A.T + (L * s) @ L.T
+    assert np.linalg.norm(Rl - (Wl * s) @ Wl.T) <= 1e-10 * np.linalg.norm(L @ L.T)
+    X = O.bartels_stewart(A, L @ L.T)
+    Zi, info = O.ir_chol(A, L, O.Opts(u_s="fp16", inner="adi", tau_ir=1e-13))
+    assert info.converged
+    assert rel(Zi @ Zi.T, X) <= 1e-10
