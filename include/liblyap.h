@@ -48,8 +48,18 @@ extern "C" {
 /* Solver precisions u_s (Table 1.1); u = u_r = u_c = FP64 in this library. */
 typedef enum { LYAP_FP64 = 0, LYAP_FP32 = 1, LYAP_FP16 = 2, LYAP_BF16 = 3 } lyap_prec_t;
 
-/* Newton scaling (Sec. 3): Frobenius (the paper's choice, Sec. 4), determinantal, none. */
-typedef enum { LYAP_SCALE_FROB = 0, LYAP_SCALE_DET = 1, LYAP_SCALE_NONE = 2 } lyap_scaling_t;
+/* Newton scaling (Sec. 3.1): Frobenius (the paper's choice, Sec. 4), determinantal, none,
+ * 2-norm mu = (||A_k^-1||_2 / ||A_k||_2)^1/2 and spectral mu = (rho(A_k^-1) / rho(A_k))^1/2.
+ * The last two are estimated on the GPU in FP32: the 2-norms by 12 power steps on M^T M,
+ * the spectral radii by the geometric mean of ||M v|| / ||v|| over steps 13..24 of a power
+ * iteration on M (a few per cent, which only steers the scaling). */
+typedef enum {
+  LYAP_SCALE_FROB = 0,
+  LYAP_SCALE_DET = 1,
+  LYAP_SCALE_NONE = 2,
+  LYAP_SCALE_NORM2 = 3,
+  LYAP_SCALE_SPECTRAL = 4
+} lyap_scaling_t;
 
 typedef struct lyap_ctx lyap_ctx_t;
 

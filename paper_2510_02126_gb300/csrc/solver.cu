@@ -67,7 +67,7 @@ static T* P(Buf& b) { return reinterpret_cast<T*>(b.p); }
 
 // Device-side state of one sign-Newton run (read back by the host after each step).
 struct NewtonState {
-  double ssA, ssX, maxX, mu, ssA1, ssD, ssE, stopv, delta, delta_prev, logdet;
+  double ssA, ssX, maxX, mu, ssA1, ssD, ssE, stopv, delta, delta_prev, logdet, nrmA, nrmX;
   double meas[64];
   int scaling_on, fired, prev_unscaled, done, k, eX, status, pad;
 };
@@ -109,6 +109,7 @@ struct lyap_ctx {
   lyap::Buf At, Ct, ZY, adjT;
   lyap::Buf tl;  // trace loss: C Z and C Z diag(D)
   lyap::Buf Hf;  // FP32 copy of the residual core for its range finder
+  lyap::Buf pnw; // power-iteration vectors of the 2-norm / spectral-radius scalings
   lyap::Buf eigWork32, eigBig, eigX, eigR, eigS, eigHX, eigE, eigLam, eigRed, eigW, eigPv, eigInt;
   void* hpin = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -188,6 +189,7 @@ __global__ void newton_mu_kernel(NewtonState* st, int n, int scaling, int store1
   if (st->scaling_on) {
     if (scaling == LYAP_SCALE_FROB) mu = sqrt(sqrt(st->ssX) / sqrt(st->ssA));
     else if (scaling == LYAP_SCALE_DET) mu = exp(-st->logdet / (double)n);
+    else if (scaling == LYAP_SCALE_NORM2 || scaling == LYAP_SCALE_SPECTRAL) mu = sqrt(st->nrmX / st->nrmA);
   }
   if (!isfinite(mu) || !(mu > 0.0) || !isfinite(st->ssX)) atomicCAS(&st->status, 0, LYAP_ERR_NONFINITE);
   st->mu = mu;
@@ -242,6 +244,89 @@ newton_update_kernel(int n, const T* __restrict__ Ak, const T* __restrict__ X, c
     part[threadIdx.x * RED_BLOCKS + blockIdx.x] = t;
   }
 }
+// ---- 2-norm and spectral-radius estimates of a row-major n x n matrix M (FP32 power
+// iteration; v, u: n floats; part: PN_SPLIT x n floats; hist: PN_STEPS + 1 doubles)
+constexpr int PN_STEPS_NORM2 = 12;     // power steps on M^T M
+constexpr int PN_STEPS_SPECTRAL = 24;  // power steps on M (the geometric mean of the second half)
+constexpr int PN_SPLIT = 16;           // row chunks of the M^T u partial sums
+// v = a fixed non-degenerate start; hist[0] = ||v||^2
+__global__ void pn_init_kernel(int n, float* __restrict__ v, double* __restrict__ hist) {
+  __shared__ double red[32];
+  double t = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const float x = 1.0f + 0.01f * (float)(j % 7);
+    v[j] = x;
+    t += (double)x * x;
+  }
+  t = warp_sum(t);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k];
+    hist[0] = s;
+  }
+}
+// u = M P v / ||v|| (one warp per row; (P v)_p = v[cmap[p]], cmap == NULL: identity)
+template <typename T>
+__global__ void __launch_bounds__(256) pn_mv_kernel(const T* __restrict__ M, int n, const int* __restrict__ cmap,
+                                                    const float* __restrict__ v, const double* __restrict__ vn2,
+                                                    float* __restrict__ u) {
+  const int lane = threadIdx.x & 31;
+  const float inv = (float)(1.0 / sqrt(*vn2));
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += (gridDim.x * blockDim.x) >> 5) {
+    const T* row = M + (int64_t)i * n;
+    float t = 0.f;
+    for (int p = lane; p < n; p += 32) t = fmaf((float)row[p], v[cmap ? cmap[p] : p], t);
+    t = warp_sum(t);
+    if (lane == 0) u[i] = t * inv;
+  }
+}
+// part[s n + j] = sum over the rows i of chunk s of M[i, j] u_i (M^T u in PN_SPLIT row chunks)
+template <typename T>
+__global__ void __launch_bounds__(256) pn_mtv_kernel(const T* __restrict__ M, int n, const float* __restrict__ u,
+                                                     float* __restrict__ part) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int s = blockIdx.y, i0 = (int)((int64_t)n * s / PN_SPLIT), i1 = (int)((int64_t)n * (s + 1) / PN_SPLIT);
+  float t = 0.f;
+  for (int i = i0; i < i1; ++i) t = fmaf((float)M[(int64_t)i * n + j], u[i], t);
+  part[(int64_t)s * n + j] = t;
+}
+// v = sum of the nparts rows of part (fixed order); out = ||v||^2 (one CTA)
+__global__ void pn_sum_kernel(const float* __restrict__ part, int n, int nparts, float* __restrict__ v,
+                              double* __restrict__ out) {
+  __shared__ double red[32];
+  double t = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    float x = 0.f;
+    for (int s = 0; s < nparts; ++s) x += part[(int64_t)s * n + j];
+    v[j] = x;
+    t += (double)x * x;
+  }
+  t = warp_sum(t);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k];
+    *out = s;
+  }
+}
+// *est from the recorded norms: 2-norm ||M^T M v^|| ^ (1/2) of the last step; spectral
+// radius exp(mean of log ||M v^|| over the second half of the steps)
+__global__ void pn_final_kernel(const double* __restrict__ hist, int steps, int spectral, double* __restrict__ est) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (!spectral) {
+    *est = sqrt(sqrt(hist[steps]));
+  } else {
+    double l = 0.0;
+    const int h = steps / 2;
+    for (int k = steps - h + 1; k <= steps; ++k) l += 0.5 * log(hist[k]);
+    *est = exp(l / h);
+  }
+}
+
 __global__ void newton_sums_kernel(const double* __restrict__ part, int nb, NewtonState* st) {
   // fixed-order sums of the three partial vectors
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -783,6 +868,35 @@ struct NewtonOpts {
   double tau, scale_off, rank_tol, rho;
 };
 
+// ||M||_2 (spectral = false; 12 power steps on M^T M) or the spectral radius of M P
+// (spectral = true; (P v)_p = v[cmap[p]], cmap == NULL: P = I) of the row-major n x n M,
+// written to *est on the device (FP32 iteration, FP64 norms).
+template <typename T>
+static int norm_estimate(Ctx& C, const T* M, int n, const int* cmap, bool spectral, double* est) {
+  const int steps = spectral ? PN_STEPS_SPECTRAL : PN_STEPS_NORM2;
+  const size_t hb = (size_t)(PN_STEPS_SPECTRAL + 2) * 8;
+  LYAP_TRY(ensure(C.pnw, hb + (size_t)(2 + PN_SPLIT) * n * 4 + 64));
+  double* hist = P<double>(C.pnw);
+  float* v = reinterpret_cast<float*>(static_cast<char*>(C.pnw.p) + hb);
+  float* u = v + n;
+  float* part = u + n;
+  pn_init_kernel<<<1, 1024, 0, C.s>>>(n, v, hist);
+  const unsigned rows = (unsigned)std::min<int64_t>(4096, ceil_div((int64_t)n, 8));
+  for (int k = 1; k <= steps; ++k) {
+    pn_mv_kernel<T><<<rows, 256, 0, C.s>>>(M, n, spectral ? cmap : nullptr, v, hist + k - 1, u);
+    if (spectral) {
+      pn_sum_kernel<<<1, 1024, 0, C.s>>>(u, n, 1, v, hist + k);
+    } else {
+      pn_mtv_kernel<T><<<dim3((unsigned)ceil_div((int64_t)n, 256), PN_SPLIT), 256, 0, C.s>>>(M, n, u, part);
+      pn_sum_kernel<<<1, 1024, 0, C.s>>>(part, n, PN_SPLIT, v, hist + k);
+    }
+  }
+  pn_final_kernel<<<1, 32, 0, C.s>>>(hist, steps, spectral ? 1 : 0, est);
+  LYAP_CUDA_TRY(cudaGetLastError());
+  lyap_count_launch(2 + steps * (spectral ? 2 : 3));
+  return LYAP_OK;
+}
+
 // Run the sign-Newton factor iteration on Z (working precision, n x c0 in C.Zw, column-major).
 // compute == true: compute and store the inverse sequence from the working
 // matrix in C.A0 (row-major, already scaled); else replay the stored sequence.
@@ -807,6 +921,9 @@ static int newton_run(Ctx& C, int n, int c0, bool ldlt, const NewtonOpts& o, boo
   T* Acur = P<T>(C.A0);
   T* Anext = P<T>(C.A1);
   bool finished = false;
+  // the 2-norm / spectral scalings need norm estimates while scaling is on (the host learns
+  // of its switch-off from the state read back after each step)
+  bool est_norms = compute && (o.scaling == LYAP_SCALE_NORM2 || o.scaling == LYAP_SCALE_SPECTRAL);
   const int ce = C.store_ckpt;
   if (!compute && ce) LYAP_CUDA_TRY(cudaMemsetAsync(C.gj.status, 0, sizeof(int), C.s));
   for (int kk = 0; kk < K; ++kk) {
@@ -836,6 +953,11 @@ static int newton_run(Ctx& C, int n, int c0, bool ldlt, const NewtonOpts& o, boo
         LYAP_TRY(sumsq<T>(X, n, n, n, &st->ssX, P<double>(C.part), C.s));
         LYAP_TRY(maxabs<T>(X, n, n, n, &st->maxX, P<double>(C.part), C.s));
         if (o.scaling == LYAP_SCALE_DET) LYAP_TRY(pivot_logs(C.gj, &st->logdet, C.s));
+        if (est_norms) {
+          const bool sp = (o.scaling == LYAP_SCALE_SPECTRAL);
+          LYAP_TRY(norm_estimate<T>(C, Acur, n, nullptr, sp, &st->nrmA));
+          LYAP_TRY(norm_estimate<T>(C, X, n, perm, sp, &st->nrmX));
+        }
         newton_mu_kernel<<<1, 1, 0, C.s>>>(st, n, o.scaling, is16(o.prec) ? 1 : 0);
       } else {
         newton_recorded_mu_kernel<<<1, 1, 0, C.s>>>(st, P<double>(C.dmu), P<int>(C.dex), kk);
@@ -917,6 +1039,7 @@ static int newton_run(Ctx& C, int n, int c0, bool ldlt, const NewtonOpts& o, boo
         if (tcs) return tcs;
       }
       if (info && kk < 64) info->mu[kk] = hst.mu;
+      if (!hst.scaling_on) est_norms = false;
       if (gjs) return gjs;
       if (qrs) return qrs;
       if (hst.status) return hst.status;
@@ -1035,7 +1158,7 @@ int lyap_ctx_destroy(lyap_ctx_t* C) {
                 &C->Lm, &C->Zs, &C->Zbest, &C->G, &C->gram, &C->ysol, &C->ybest, &C->ytmp, &C->Lw, &C->Sd,
                 &C->Vs, &C->Lst, &C->Rtau, &C->Bm, &C->VB, &C->qrBar, &C->qrStatus, &C->qrCand, &C->qrNorms, &C->qrPiv, &C->qrRdiag, &C->qrWork,
                 &C->qrRank, &C->eigWork32, &C->eigBig, &C->eigX, &C->eigR, &C->eigS, &C->eigHX, &C->eigE, &C->eigLam,
-                &C->eigRed, &C->eigW, &C->eigPv, &C->eigInt, &C->At, &C->Ct, &C->ZY, &C->adjT, &C->Hf, &C->tl, &C->inv1};
+                &C->eigRed, &C->eigW, &C->eigPv, &C->eigInt, &C->At, &C->Ct, &C->ZY, &C->adjT, &C->Hf, &C->tl, &C->inv1, &C->pnw};
   for (Buf* b : all) free_buf(*b);
   for (lyap_ctx* w : C->pool) lyap_ctx_destroy(w);
   for (cudaStream_t st : C->pool_streams) cudaStreamDestroy(st);
@@ -1499,7 +1622,7 @@ static int check_problem(const Problem& pb, const lyap_opts_t* o, double* Z, int
   if (!pb.A || !pb.L || !o || !Z) return LYAP_ERR_ARG;
   if (pb.n <= 0 || pb.m <= 0 || pb.lda < pb.n || pb.ldl < pb.n || ldz < pb.n || z_cap <= 0) return LYAP_ERR_ARG;
   if (pb.S && pb.lds < pb.m) return LYAP_ERR_ARG;
-  if (o->u_s < 0 || o->u_s > 3 || o->scaling < 0 || o->scaling > 2 || o->kmax <= 0 || o->imax < 0) return LYAP_ERR_ARG;
+  if (o->u_s < 0 || o->u_s > 3 || o->scaling < 0 || o->scaling > 4 || o->kmax <= 0 || o->imax < 0) return LYAP_ERR_ARG;
   if (o->u != LYAP_FP64 || o->u_r != LYAP_FP64 || o->u_c != LYAP_FP64) {
     lyap_set_error_message("only u = u_r = u_c = LYAP_FP64 is implemented", __FILE__, __LINE__);
     return LYAP_ERR_ARG;

@@ -16,8 +16,9 @@ from . import build_lib
 
 FP64, FP32, FP16, BF16 = 0, 1, 2, 3
 PREC = {"fp64": FP64, "fp32": FP32, "fp16": FP16, "bf16": BF16}
-SCALE_FROB, SCALE_DET, SCALE_NONE = 0, 1, 2
-SCALING = {"frob": SCALE_FROB, "det": SCALE_DET, "none": SCALE_NONE}
+SCALE_FROB, SCALE_DET, SCALE_NONE, SCALE_NORM2, SCALE_SPECTRAL = 0, 1, 2, 3, 4
+SCALING = {"frob": SCALE_FROB, "det": SCALE_DET, "none": SCALE_NONE, "norm2": SCALE_NORM2,
+           "spectral": SCALE_SPECTRAL}
 
 PHASES = ["invert", "newton", "factor", "compress", "resfac", "eig", "solupt", "other", "eig_refine", "spare9",
           "spare10", "spare11"]

@@ -317,3 +317,32 @@ def test_ir_ldlt_indefinite_n4096_fp32():
     assert rel((Zn * Dn) @ Zn.T, X) <= 1e-10
     assert O.residual_eq41(A, Zn, W, Dn) <= 1e-12
     assert abs(info.res_final - O.residual_eq41(A, Zn, W, Dn)) <= 1e-3 * info.res_final
+
+
+@pytest.mark.parametrize("scaling", ["norm2", "spectral"])
+def test_sign_solve_norm2_and_spectral_scaling(scaling):
+    # the 2-norm and spectral scalings of Sec. 3.1: the GPU estimates ||.||_2 and rho(.) by
+    # power iteration, the oracle takes them exactly.  On the nonsymmetric convection-
+    # diffusion matrix (n = 144): mu_k (k >= 1; mu_0 also carries the power-of-two prescale
+    # of A_0) within 5% while scaling is on, the Newton count within one step, and the same
+    # solution; FP16-inner refinement with this scaling converges to 1e-12
+    d = gen.convdiff_shifted(grid=12, m=2)
+    A, L = d["A"], d["L"]
+    W = L @ L.T
+    X = O.bartels_stewart(A, W)
+    rec = O.newton_sequence(A, O.Opts(u_s="fp64", scaling=scaling))
+    Z, _, info = lib().sign_solve(T(A), T(L), u_s="fp64", scaling=scaling)
+    assert abs(info.newton_max - len(rec.mus)) <= 1
+    mu = list(info.mu)
+    checked = 0
+    for k in range(1, min(info.newton_max, len(rec.mus))):
+        if rec.mus[k] == 1.0:
+            break
+        assert abs(mu[k] - rec.mus[k]) <= 0.05 * rec.mus[k], (k, mu[k], rec.mus[k])
+        checked += 1
+    assert checked >= 1
+    assert rel(N(Z) @ N(Z).T, X) <= 1e-10
+    Z2, _, info2 = lib().solve_ir(T(A), T(L), u_s="fp16", scaling=scaling, tau_ir=1e-12, imax=30)
+    assert info2.converged, info2.as_dict()
+    assert rel(N(Z2) @ N(Z2).T, X) <= 1e-10
+    assert O.residual_eq41(A, N(Z2), W) <= 1e-12
