@@ -441,6 +441,8 @@ def run_case(args):
                         Newton steps) + lyap_adjoint of l = trace(C X C^T) (p = 2 family, m = 4,
                         C 4 x n): times, and central differences of FP64 sign-Newton losses on k
                         (default 20) random directions of A and L (relative errors)
+    kappa_sign          kappa_sign(B) of B = [[A, W], [0, -A^T]] (lyap_kappa_sign) for the n = 1024
+                        workload and the block-normal family at n = 1024, p = 1..4
     config1             FP64 sign-Newton on the 8 x 8-grid Laplacian (n = 64, determinantal scaling,
                         Frobenius stop 1e-12 n): microseconds per solve (CUDA events)"""
     import numpy as np
@@ -674,6 +676,24 @@ def run_case(args):
                           "fd_precision": "fp64 sign-Newton losses",
                           "max_rel_err_dA": mx(rel_A), "max_rel_err_dL": mx(rel_L),
                           "max_err_dA_over_grad_norm": mx(nrm_A), "max_err_dL_over_grad_norm": mx(nrm_L)}))
+        return 0
+    elif kind == "kappa_sign":
+        # kappa_sign(B), B = [[A, W], [0, -A^T]] (Sec. 4.2), for the n = 1024 convection-
+        # diffusion workload and the block-normal family at n = 1024, p = 1..4 (host wall clock)
+        import time
+        import lyapgen
+        cases = [("convdiff n=1024", lyapgen.convdiff_shifted())]
+        cases += [(f"normal blocks n=1024 p={p}", lyapgen.normal_blocks(n=1024, p=p, m=8, indefinite=True))
+                  for p in (1, 2, 3, 4)]
+        for name, d in cases:
+            A, L = torch.tensor(d["A"], device=dev), torch.tensor(d["L"], device=dev)
+            S = torch.tensor(d["S"], device=dev) if "S" in d else None
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = lyap.kappa_sign(A, L, S=S, power_steps=8)
+            torch.cuda.synchronize()
+            print(json.dumps({"case": "kappa_sign", "workload": name, **out, "seconds": time.perf_counter() - t0}),
+                  flush=True)
         return 0
     elif kind == "config1":
         import lyapgen

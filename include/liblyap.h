@@ -259,6 +259,24 @@ int lyap_trace_loss(lyap_ctx_t* ctx, const double* Z, int64_t n, int64_t ldz, in
                     const double* Cm, int64_t ldc, int64_t q, double* loss, double* dC, int64_t lddc);
 
 /*
+ * kappa_sign(B) in the Frobenius norm for B = [[A, W], [0, -A^T]], W = L L^T (S == NULL)
+ * or L S L^T: the condition of the matrix sign function that the sign-Newton iteration
+ * computes (sign(B) = [[-I, 2X], [0, I]]), the indicator Sec. 4.2 uses for the accuracy of
+ * the Newton solver.  An FP64 Newton iteration on B (order 2n, Frobenius scaling) keeps its
+ * inverses; the Frechet derivative L(B, E) is the derivative of that iteration and its
+ * adjoint uses the transposed inverses; ||L||_F is estimated by power_steps (1..100) steps
+ * of the power method on L^* L from a fixed pseudo-random start (a lower bound, typically
+ * within a few per cent).  Out (host): *kappa = ||L||_F ||B||_F / ||sign(B)||_F; *lnorm =
+ * ||L||_F (may be NULL); *newton_steps = iterations on B (may be NULL).  A, L, S: device,
+ * column-major, as lyap_solve_ir.  Workspace: about (K + 5) (2n)^2 doubles (K Newton
+ * steps), allocated and freed by the call (LYAP_ERR_NOMEM when it does not fit); n <= 16384.
+ * Cost: K inversions of order 2n and 4 K power_steps FP64 products of order 2n.
+ */
+int lyap_kappa_sign(lyap_ctx_t* ctx, const double* A, int64_t n, int64_t lda, const double* L, int64_t ldl,
+                    int64_t m, const double* S, int64_t lds, int power_steps, double* kappa, double* lnorm,
+                    int* newton_steps);
+
+/*
  * FP64 matrix product C = alpha op(A) op(B) + beta C (op = 'N' or 'T'; column-major DEVICE
  * operands, beta == 0 does not read C): the products of the FP64 steps of the method -- A Z and
  * the core matrices T P T^T, Gamma J Gamma^T of Fragments ResFacChol / SolUptChol (Sec. 2.1),
@@ -270,7 +288,8 @@ int lyap_trace_loss(lyap_ctx_t* ctx, const double* Z, int64_t n, int64_t ldz, in
  *             and the 36 leading pairs are summed in FP64.  Error about 2^-50 K max|a| max|b|
  *             per entry (row / column maxima), the order of an FP64 product's bound.
  *   method 0: 2 for products of at least 3e7 multiply-adds with k >= 128 and at least 48
- *             output tiles of 128 x 32, 1 otherwise.
+ *             (output tile of 128 x 32, K range) pairs -- outputs of fewer than 74 tiles split
+ *             K into up to 16 ranges of at least 256, summed in a fixed order -- 1 otherwise.
  * Synchronises the context stream; returns LYAP_ERR_TIMEOUT if a bounded device wait gave up.
  */
 int lyap_dgemm(lyap_ctx_t* ctx, char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,

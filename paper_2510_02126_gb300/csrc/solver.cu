@@ -1067,6 +1067,40 @@ static int newton_run(Ctx& C, int n, int c0, bool ldlt, const NewtonOpts& o, boo
   return LYAP_OK;
 }
 
+// ---- kappa_sign(B) for B = [[A, W], [0, -A^T]] (Sec. 4.2) ----
+// B (N x N, N = 2n, column-major) from A (lda) and W (n x n)
+__global__ void sign_block_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ W, int n,
+                                  double* __restrict__ B) {
+  const int64_t N = 2 * (int64_t)n, total = N * N;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / N, i = e - j * N;
+    double v;
+    if (i < n) v = (j < n) ? A[i + j * lda] : W[i + (j - n) * n];
+    else v = (j < n) ? 0.0 : -A[(j - n) + (i - n) * lda];
+    B[e] = v;
+  }
+}
+// Y = a X + b Z (N x N, contiguous); D = Y - X when D != NULL
+__global__ void axpby_kernel(int64_t total, double a, const double* __restrict__ X, double b,
+                             const double* __restrict__ Z, double* __restrict__ Y, double* __restrict__ D) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const double x = X[e], y = a * x + b * Z[e];
+    Y[e] = y;
+    if (D) D[e] = y - x;
+  }
+}
+// deterministic start of the power method: entries uniform in [-1, 1) from a counter hash
+// (splitmix64 of seed + index)
+__global__ void hash_fill_kernel(int64_t total, uint64_t seed, double* __restrict__ E) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = seed + 0x9e3779b97f4a7c15ull * (uint64_t)(e + 1);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    z ^= z >> 31;
+    E[e] = (double)(z >> 11) * 0x1.0p-52 - 1.0;
+  }
+}
+
 }  // namespace lyap
 
 // ===========================================================================
@@ -2094,6 +2128,140 @@ int lyap_residual(lyap_ctx_t* C, const double* A, int64_t n, int64_t lda, const 
                    &ro));
   *res_out = ro.res;
   return LYAP_OK;
+}
+
+// kappa_sign(B) in the Frobenius norm, B = [[A, W], [0, -A^T]] (Sec. 4.2).  The FP64 Newton
+// iteration on B (Frobenius scaling until delta_k < 1e-2, stopped one step after delta_k <= 1e-8)
+// keeps its inverses X_k^{-1} and mu_k; the Frechet derivative L(B, E) is the derivative of that
+// iteration, E <- (mu_k E - mu_k^{-1} X_k^{-1} E X_k^{-1}) / 2 (exact in the limit: the fixed
+// mu_k sequence converges for B + tE too), its adjoint L(B^T, .) the same with transposed
+// inverses; ||L||_F comes from the power method on L^* L.
+int lyap_kappa_sign(lyap_ctx_t* C, const double* A, int64_t n, int64_t lda, const double* L, int64_t ldl, int64_t m,
+                    const double* S, int64_t lds, int power_steps, double* kappa, double* lnorm, int* newton_steps) {
+  if (!C || !A || !L || !kappa || n <= 0 || m <= 0 || lda < n || ldl < n || (S && lds < m) || power_steps < 1 ||
+      power_steps > 100 || n > 16384)
+    return LYAP_ERR_ARG;
+  Ctx& X = *C;
+  Problem pb{A, (int)n, lda, L, ldl, (int)m, S, lds};
+  LYAP_TRY(ensure(X.scal, 4096));
+  LYAP_TRY(ensure(X.part, (size_t)4 * RED_BLOCKS * 8));
+  double* Lw = nullptr;
+  double* sd = nullptr;
+  bool indef = false;
+  LYAP_TRY(prepare_rhs(X, pb, &Lw, &sd, &indef));
+  const int64_t N = 2 * n;
+  const size_t NN = (size_t)N * N;
+  // workspace: iterate, next iterate, E, two temporaries (5 N^2), W (n^2) and L S (n m); the
+  // inverses of the iteration in their own allocations; all freed on return
+  double* ws = nullptr;
+  if (cudaMalloc(&ws, (5 * NN + (size_t)n * n + (size_t)n * m) * 8) != cudaSuccess) {
+    cudaGetLastError();
+    lyap_set_error_message("device allocation failed (kappa_sign workspace)", __FILE__, __LINE__);
+    return LYAP_ERR_NOMEM;
+  }
+  std::vector<double*> inv;
+  std::vector<double> mus;
+  auto run = [&]() -> int {
+    double* Xc = ws;
+    double* Xn = ws + NN;
+    double* E = ws + 2 * NN;
+    double* T1 = ws + 3 * NN;
+    double* T2 = ws + 4 * NN;
+    double* W = ws + 5 * NN;
+    double* LS = W + (size_t)n * n;
+    double* sc = P<double>(X.scal) + 40;
+    double* part = P<double>(X.part);
+    LYAP_TRY((copy_cast<double, double>(Lw, n, m, n, LS, n, 1.0, X.s)));
+    if (sd) LYAP_TRY(scale_cols<double>(LS, n, m, n, sd, X.s));
+    LYAP_TRY(gemm<double>('N', 'T', n, n, m, 1.0, LS, n, Lw, n, 0.0, W, n, X.s));
+    const unsigned g = (unsigned)std::min<int64_t>(4096, ceil_div((int64_t)NN, 256));
+    sign_block_kernel<<<g, 256, 0, X.s>>>(A, lda, W, (int)n, Xc);
+    LYAP_CUDA_TRY(cudaGetLastError());
+    lyap_count_launch();
+    double h[2];
+    LYAP_TRY(sumsq<double>(Xc, N, N, N, sc, part, X.s));
+    LYAP_TRY(sync_read(X, sc, h, sizeof(double)));
+    const double nB = std::sqrt(h[0]);
+    bool scaling = true;
+    int after = -1;
+    for (int k = 0; k < 64; ++k) {
+      double* Ik = nullptr;
+      if (cudaMalloc(&Ik, NN * 8) != cudaSuccess) {
+        cudaGetLastError();
+        lyap_set_error_message("device allocation failed (kappa_sign inverses)", __FILE__, __LINE__);
+        return LYAP_ERR_NOMEM;
+      }
+      inv.push_back(Ik);
+      LYAP_TRY(lyap_invert(C, Xc, N, N, LYAP_FP64, Ik, N, nullptr, nullptr));
+      double mu = 1.0;
+      if (scaling) {
+        LYAP_TRY(sumsq<double>(Xc, N, N, N, sc, part, X.s));
+        LYAP_TRY(sumsq<double>(Ik, N, N, N, sc + 1, part, X.s));
+        LYAP_TRY(sync_read(X, sc, h, sizeof(h)));
+        mu = std::sqrt(std::sqrt(h[1]) / std::sqrt(h[0]));
+        if (!std::isfinite(mu) || !(mu > 0.0)) return LYAP_ERR_NONFINITE;
+      }
+      mus.push_back(mu);
+      axpby_kernel<<<g, 256, 0, X.s>>>((int64_t)NN, 0.5 * mu, Xc, 0.5 / mu, Ik, Xn, T1);
+      LYAP_CUDA_TRY(cudaGetLastError());
+      lyap_count_launch();
+      LYAP_TRY(sumsq<double>(T1, N, N, N, sc, part, X.s));
+      LYAP_TRY(sumsq<double>(Xn, N, N, N, sc + 1, part, X.s));
+      LYAP_TRY(sync_read(X, sc, h, sizeof(h)));
+      std::swap(Xc, Xn);
+      const double delta = std::sqrt(h[0] / h[1]);
+      if (!std::isfinite(delta)) return LYAP_ERR_NONFINITE;
+      if (after >= 0 && k >= after) break;
+      if (after < 0 && delta <= 1e-8) after = k + 1;
+      if (scaling && delta < 1e-2) scaling = false;
+      if (k == 63) {
+        lyap_set_error_message("Newton iteration on [[A, W], [0, -A^T]] did not converge", __FILE__, __LINE__);
+        return LYAP_ERR_NOCONV;
+      }
+    }
+    LYAP_TRY(sumsq<double>(Xc, N, N, N, sc, part, X.s));
+    LYAP_TRY(sync_read(X, sc, h, sizeof(double)));
+    const double nS = std::sqrt(h[0]);
+    const int K = (int)inv.size();
+    // the derivative of the iteration applied to E in place (adjoint: transposed inverses)
+    auto apply = [&](bool adj) -> int {
+      for (int k = 0; k < K; ++k) {
+        const char t = adj ? 'T' : 'N';
+        LYAP_TRY(gemm<double>(t, 'N', N, N, N, 1.0, inv[k], N, E, N, 0.0, T1, N, X.s));
+        LYAP_TRY(gemm<double>('N', t, N, N, N, 1.0, T1, N, inv[k], N, 0.0, T2, N, X.s));
+        axpby_kernel<<<g, 256, 0, X.s>>>((int64_t)NN, 0.5 * mus[k], E, -0.5 / mus[k], T2, E, nullptr);
+        LYAP_CUDA_TRY(cudaGetLastError());
+        lyap_count_launch();
+      }
+      return LYAP_OK;
+    };
+    hash_fill_kernel<<<g, 256, 0, X.s>>>((int64_t)NN, 0x2510021260ull, E);
+    LYAP_CUDA_TRY(cudaGetLastError());
+    lyap_count_launch();
+    double gam = 0.0;
+    for (int it = 0; it < power_steps; ++it) {
+      // E <- E / ||E||_F; gamma = ||L(B, E)||_F; E <- L^*(B, L(B, E))
+      LYAP_TRY(sumsq<double>(E, N, N, N, sc, part, X.s));
+      LYAP_TRY(sync_read(X, sc, h, sizeof(double)));
+      if (!(h[0] > 0.0)) break;
+      axpby_kernel<<<g, 256, 0, X.s>>>((int64_t)NN, 1.0 / std::sqrt(h[0]), E, 0.0, E, E, nullptr);
+      lyap_count_launch();
+      LYAP_TRY(apply(false));
+      LYAP_TRY(sumsq<double>(E, N, N, N, sc, part, X.s));
+      LYAP_TRY(sync_read(X, sc, h, sizeof(double)));
+      gam = std::max(gam, std::sqrt(h[0]));
+      LYAP_TRY(apply(true));
+    }
+    *kappa = gam * nB / nS;
+    if (lnorm) *lnorm = gam;
+    if (newton_steps) *newton_steps = K;
+    return LYAP_OK;
+  };
+  const int rc = run();
+  cudaStreamSynchronize(X.s);
+  for (double* p : inv) cudaFree(p);
+  cudaFree(ws);
+  return rc;
 }
 
 int lyap_dgemm(lyap_ctx_t* C, char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,

@@ -94,6 +94,8 @@ SIGNATURES = {
                                C.POINTER(LyapInfo)]),
     "lyap_dgemm": (C.c_int, [_P, C.c_char, C.c_char, _I64, _I64, _I64, _D, _P, _I64, _P, _I64, _D, _P, _I64, C.c_int]),
     "lyap_trace_loss": (C.c_int, [_P, _P, _I64, _I64, _I64, _P, _P, _I64, _I64, C.POINTER(_D), _P, _I64]),
+    "lyap_kappa_sign": (C.c_int, [_P, _P, _I64, _I64, _P, _I64, _I64, _P, _I64, C.c_int, C.POINTER(_D),
+                                  C.POINTER(_D), C.POINTER(C.c_int)]),
     "lyap_rank_trunc": (C.c_int, [_P, _P, _I64, _I64, _I64, _D, C.POINTER(_I64)]),
     "lyap_sym_eig": (C.c_int, [_P, _P, _I64, _I64, _P, _P, _I64, C.c_int]),
     "lyap_last_error": (C.c_char_p, []),
@@ -293,6 +295,20 @@ def adjoint(A, L, Z, Cm, S=None, D=None, opts=None, want=("dA", "dL", "dS"), fac
     return {"dA": dA, "dL": dL, "dS": dS, "Zy": Zy[:, : ry.value] if Zy is not None else None, "info": info}
 
 
+def kappa_sign(A, L, S=None, power_steps=8):
+    """kappa_sign(B) in the Frobenius norm for B = [[A, L S L^T], [0, -A^T]] (lyap_kappa_sign):
+    returns {"kappa", "lnorm", "newton_steps"}."""
+    ctx = context()
+    A, L = _cm(A), _cm(L)
+    n, m = L.shape
+    Sc = _cm(S) if S is not None else None
+    kap, ln, ks = _D(0.0), _D(0.0), C.c_int(0)
+    _check(ctx.lib.lyap_kappa_sign(ctx.h, _P(A.data_ptr()), n, n, _P(L.data_ptr()), n, m,
+                                   _P(Sc.data_ptr()) if Sc is not None else None, m, int(power_steps),
+                                   C.byref(kap), C.byref(ln), C.byref(ks)), allow_warn=False)
+    return {"kappa": kap.value, "lnorm": ln.value, "newton_steps": ks.value}
+
+
 def trace_loss_value(Z, Cm, D=None, want_grad=False):
     """l = trace(C X C^T) for X = Z diag(D) Z^T, and dl/dC = 2 C X when want_grad
     (lyap_trace_loss).  Returns (loss, dC or None)."""
@@ -447,4 +463,5 @@ lyap_solve_ir_batched = solve_ir_batched
 lyap_rank_trunc = rank_trunc
 lyap_trace_loss = trace_loss_value
 lyap_dgemm = dgemm
+lyap_kappa_sign = kappa_sign
 lyap_sym_eig = sym_eig

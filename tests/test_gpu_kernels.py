@@ -265,3 +265,34 @@ def test_dgemm_zero_and_empty():
     C0 = np.full((64, 30), 3.0)
     C = N(lib().dgemm(T(np.zeros((64, 0))), T(np.zeros((0, 30))), beta=1.0, C=T(C0), method="tensor"))
     assert np.array_equal(C, C0)
+
+
+# ------------------------------------------------ condition of the sign function
+
+@pytest.mark.parametrize("n,indef", [(6, False), (12, True)])
+def test_kappa_sign_matches_oracle(n, indef):
+    # lyap_kappa_sign (derivative of the Newton iteration on B, power method on L^* L)
+    # against the oracle's exact kappa_sign(B) (Kronecker matrix of the Frechet derivative)
+    d = gen.normal_blocks(n=n, p=1, m=2, indefinite=indef, seed=gen.SEED_BASE + 60 + n)
+    A, L = d["A"], d["L"]
+    S = d["S"] if indef else None
+    W = L @ (S if indef else np.eye(2)) @ L.T
+    ref = O.kappa_sign_fro(O.sign_block(A, W))
+    out = lib().kappa_sign(T(A), T(L), S=T(S) if indef else None, power_steps=20)
+    assert 0.95 * ref <= out["kappa"] <= ref * (1 + 1e-6), (out, ref)
+    assert out["newton_steps"] >= 3
+
+
+def test_kappa_sign_scaling_and_similarity_invariance():
+    # kappa_sign(B) is invariant under A -> 4 A, L -> 2 L (B -> 4 B: exact in binary, and the
+    # Frobenius scaling of the Newton iteration absorbs it) and under an orthogonal change of
+    # basis (A -> Q^T A Q, L -> Q^T L); n = 100 convection-diffusion
+    d = gen.convdiff_shifted(grid=10, m=2)
+    A, L = d["A"], d["L"]
+    k0 = lib().kappa_sign(T(A), T(L), power_steps=20)
+    k1 = lib().kappa_sign(T(4.0 * A), T(2.0 * L), power_steps=20)
+    assert abs(k1["kappa"] - k0["kappa"]) <= 1e-8 * k0["kappa"]
+    assert k1["newton_steps"] == k0["newton_steps"]
+    Q, _ = np.linalg.qr(gen.rng(61).standard_normal(A.shape))
+    k2 = lib().kappa_sign(T(Q.T @ A @ Q), T(Q.T @ L), power_steps=20)
+    assert abs(k2["kappa"] - k0["kappa"]) <= 0.02 * k0["kappa"], (k0, k2)
