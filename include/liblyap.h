@@ -105,8 +105,29 @@ typedef struct {
                            solution update (Algorithms IR-Chol / IR-LDLT, Table 2.1): this
                            library implements u = u_r = u_c = LYAP_FP64 (the configuration the
                            analysis of Sec. 2 targets); any other value returns LYAP_ERR_ARG */
-  int reserved[3];
+  int inner;            /* lyap_inner_t: inner solver of the refinement (and of lyap_sign_solve) */
+  int adi_shifts;       /* low-rank ADI: number of cyclic real shifts (<= 0: 8; at most kmax) */
+  int adi_maxit;        /* low-rank ADI: step limit per solve (<= 0: 200) */
+  double adi_tol;       /* low-rank ADI: stop once ||W_j S W_j^T||_F <= adi_tol ||L S L^T||_F
+                           (<= 0: max(10 u_s, 1e-14)) */
 } lyap_opts_t;
+
+/*
+ * Inner solvers.  LYAP_INNER_SIGN: the scaled sign-function Newton iteration (Sec. 3).
+ * LYAP_INNER_ADI: low-rank ADI (Sec. 5 names ADI-based solvers as alternatives inside the
+ * same refinement framework; no counterpart in the paper's experiments) with real cyclic
+ * shifts p_j = -b (a/b)^((2j-1)/(2 adi_shifts)), a = 1/||A^-1||_2 and b = ||A||_2 estimated
+ * by power iteration: V_j = (A + p_j I)^-1 W_{j-1}, W_j = W_{j-1} - 2 p_j V_j (W_0 = L),
+ * Z_j = [Z_{j-1}, sqrt(-2 p_j) V_j] (Cholesky) or [Z_{j-1}, V_j] with weights -2 p_j S
+ * (LDL^T), so that the residual of Z_j is W_j S W_j^T.  The shifted inverses are computed
+ * once at u_s (the GJ inversion, 16-bit storage) and every correction solve reuses them,
+ * as the sign-Newton sequence (Sec. 3.4).  Real shifts suit spectra near the real axis;
+ * eigenvalues with |Im| >> |Re| converge slowly.  Checkpointing does not apply (the
+ * adi_shifts inverses are always stored).  In lyap_info_t the inner counts (newton_*) and
+ * n_inversions count the stored shifted inverses, and mu[j] holds the shift p_j (of the
+ * power-of-two prescaled A).
+ */
+typedef enum { LYAP_INNER_SIGN = 0, LYAP_INNER_ADI = 1 } lyap_inner_t;
 
 /* Phases reported in lyap_info_t.phase_ms / phase_calls / phase_flops when
  * opts.profile = 1 (LYAP_NUM_PHASES slots; the unused ones stay zero). */

@@ -110,6 +110,8 @@ struct lyap_ctx {
   lyap::Buf tl;  // trace loss: C Z and C Z diag(D)
   lyap::Buf Hf;  // FP32 copy of the residual core for its range finder
   lyap::Buf pnw; // power-iteration vectors of the 2-norm / spectral-radius scalings
+  lyap::Buf adiW, adiY, adiG;  // low-rank ADI: [W, V] (working precision), weights of W, W^T W
+  std::vector<double> adi_p;   // low-rank ADI: the shifts of the stored inverses
   lyap::Buf eigWork32, eigBig, eigX, eigR, eigS, eigHX, eigE, eigLam, eigRed, eigW, eigPv, eigInt;
   void* hpin = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -324,6 +326,67 @@ __global__ void pn_final_kernel(const double* __restrict__ hist, int steps, int 
     const int h = steps / 2;
     for (int k = steps - h + 1; k <= steps; ++k) l += 0.5 * log(hist[k]);
     *est = exp(l / h);
+  }
+}
+
+// ---- low-rank ADI (real cyclic shifts) ----
+// M = A0 + p I (row-major n x n, working precision)
+template <typename T>
+__global__ void adi_shift_kernel(const T* __restrict__ A0, int n, double p, T* __restrict__ M) {
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, j = e - i * n;
+    M[e] = (T)((double)A0[e] + (i == j ? p : 0.0));
+  }
+}
+// storage exponent of inverse j (16-bit storage only), as the Newton step records it
+__global__ void adi_exp_kernel(const double* __restrict__ maxX, int j, int store16, int* __restrict__ dex,
+                               double* __restrict__ dmu) {
+  dex[j] = store16 ? pow2_exponent(*maxX) : 0;
+  dmu[j] = 1.0;
+}
+// slot j of the store = (A0 + p_j I)^{-1} (X row-major with columns permuted: X[i, pinv[c]])
+template <typename T, typename ST>
+__global__ void adi_store_kernel(int n, const T* __restrict__ X, const int* __restrict__ pinv,
+                                 const int* __restrict__ dex, int j, ST* __restrict__ Xs, int64_t ldx) {
+  const double sx = ldexp(1.0, -dex[j]);
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, c = e - i * n;
+    Xs[i * ldx + c] = (ST)((double)X[i * n + pinv[c]] * sx);
+  }
+}
+// Z[:, c0 + t] = sZ V[:, t], W[:, t] -= 2 p V[:, t] (t < m; Y = [W, V], ld n); LDL^T weights
+// y[c0 + t] = -2 p y0[t]
+template <typename T>
+__global__ void adi_step_kernel(T* __restrict__ Y, int n, int m, double p, double sZ, T* __restrict__ Z, int c0,
+                                const double* __restrict__ y0, double* __restrict__ y) {
+  const int64_t total = (int64_t)n * m;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = e / n, i = e - t * n;
+    const double v = (double)Y[i + (t + m) * (int64_t)n];
+    Z[i + (c0 + t) * (int64_t)n] = (T)(sZ * v);
+    Y[e] = (T)((double)Y[e] - 2.0 * p * v);
+    if (y && i == 0) y[c0 + t] = -2.0 * p * y0[t];
+  }
+}
+// out = ||W diag(y0) W^T||_F^2 = sum_ij (G_ij)^2 y0_i y0_j for G = W^T W (m x m; y0 == NULL: 1)
+__global__ void adi_resnorm_kernel(const double* __restrict__ G, int m, const double* __restrict__ y0,
+                                   double* __restrict__ out) {
+  __shared__ double red[32];
+  double t = 0.0;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int j = e / m, i = e - j * m;
+    const double g = G[e];
+    t += g * g * (y0 ? y0[i] * y0[j] : 1.0);
+  }
+  t = warp_sum(t);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k];
+    *out = s;
   }
 }
 
@@ -897,6 +960,160 @@ static int norm_estimate(Ctx& C, const T* M, int n, const int* cmap, bool spectr
   return LYAP_OK;
 }
 
+struct AdiOpts {
+  int shifts, maxit;
+  double tol;
+};
+
+// Low-rank ADI on Z (working precision; the right-hand side factor L in C.Zw, n x m, weights
+// in C.yv for LDL^T).  compute == true: estimate a = 1/||A0^-1||_2 and b = ||A0||_2 (power
+// iteration), place the real shifts, and store the shifted inverses (A0 + p_j I)^{-1}
+// (A0 = the prescaled working matrix in C.A0); else reuse them.  Then the iteration of
+// LYAP_INNER_ADI until ||W S W^T||_F <= tol ||L S L^T||_F, with the truncations of the Newton
+// solver whenever cols(Z) > rho n.  *c_out: columns of Z (in C.Zw, weights in C.yv).
+template <typename T>
+static int adi_run(Ctx& C, int n, int m, bool ldlt, const NewtonOpts& o, const AdiOpts& ao, bool compute, int* c_out,
+                   lyap_info_t* info) {
+  NewtonState* st = P<NewtonState>(C.state);
+  T* Z = P<T>(C.Zw);
+  double* y = P<double>(C.yv);
+  const bool s16 = is16(o.prec);
+  if (compute) {
+    const int ns = ao.shifts;
+    if (ns < 1 || ns > o.kmax) {
+      lyap_set_error_message("adi_shifts must lie in 1..kmax", __FILE__, __LINE__);
+      return LYAP_ERR_ARG;
+    }
+    mark(C, LYAP_PHASE_NEWTON);
+    T* A0 = P<T>(C.A0);
+    T* M = P<T>(C.A1);
+    LYAP_TRY(norm_estimate<T>(C, A0, n, nullptr, false, &st->nrmA));
+    mark(C, LYAP_PHASE_INVERT);
+    LYAP_TRY(invert_current<T>(C, A0, n, o.prec));
+    mark(C, LYAP_PHASE_NEWTON);
+    LYAP_TRY(norm_estimate<T>(C, (const T*)C.gj.M[C.gj.cur], n, nullptr, false, &st->nrmX));
+    NewtonState hst;
+    LYAP_TRY(sync_read(C, st, &hst, sizeof(NewtonState)));
+    int gjs = 0;
+    LYAP_TRY(sync_read(C, C.gj.status, &gjs, sizeof(int)));
+    if (gjs) return gjs;
+    const double b = hst.nrmA, a = 1.0 / hst.nrmX;
+    if (!std::isfinite(a) || !std::isfinite(b) || !(a > 0.0) || !(b > 0.0)) return LYAP_ERR_NONFINITE;
+    C.adi_p.assign(ns, 0.0);
+    for (int j = 0; j < ns; ++j) C.adi_p[j] = -b * std::pow(std::min(a, b) / b, (2.0 * j + 1.0) / (2.0 * ns));
+    for (int j = 0; j < ns; ++j) {
+      adi_shift_kernel<T><<<nblk((int64_t)n * n), 256, 0, C.s>>>(A0, n, C.adi_p[j], M);
+      lyap_count_launch();
+      mark(C, LYAP_PHASE_INVERT);
+      LYAP_TRY(invert_current<T>(C, M, n, o.prec));
+      mark(C, LYAP_PHASE_NEWTON);
+      const T* X = (const T*)C.gj.M[C.gj.cur];
+      pinv_kernel<<<nblk(n), 256, 0, C.s>>>(C.gj.perm[C.gj.cur], P<int>(C.pinv), n);
+      LYAP_TRY(maxabs<T>(X, n, n, n, &st->maxX, P<double>(C.part), C.s));
+      adi_exp_kernel<<<1, 1, 0, C.s>>>(&st->maxX, j, s16 ? 1 : 0, P<int>(C.dex), P<double>(C.dmu));
+      void* slot = inv_slot(C, j);
+      const unsigned nb = (unsigned)std::min<int64_t>(4096, ceil_div((int64_t)n * n, 256));
+      switch (o.prec) {
+        case LYAP_FP64:
+          adi_store_kernel<double, double><<<nb, 256, 0, C.s>>>(n, (const double*)X, P<int>(C.pinv), P<int>(C.dex), j,
+                                                              (double*)slot, C.store_ld);
+          break;
+        case LYAP_FP32:
+          adi_store_kernel<float, float><<<nb, 256, 0, C.s>>>(n, (const float*)X, P<int>(C.pinv), P<int>(C.dex), j,
+                                                            (float*)slot, C.store_ld);
+          break;
+        case LYAP_FP16:
+          adi_store_kernel<float, __half><<<nb, 256, 0, C.s>>>(n, (const float*)X, P<int>(C.pinv), P<int>(C.dex), j,
+                                                             (__half*)slot, C.store_ld);
+          break;
+        case LYAP_BF16:
+          adi_store_kernel<float, __nv_bfloat16><<<nb, 256, 0, C.s>>>(n, (const float*)X, P<int>(C.pinv),
+                                                                    P<int>(C.dex), j, (__nv_bfloat16*)slot,
+                                                                    C.store_ld);
+          break;
+      }
+      LYAP_CUDA_TRY(cudaGetLastError());
+      lyap_count_launch(3);
+      LYAP_TRY(sync_read(C, C.gj.status, &gjs, sizeof(int)));
+      if (gjs) return gjs;
+      if (info && j < 64) info->mu[j] = C.adi_p[j];
+    }
+    C.store_count = ns;
+  } else if ((int)C.adi_p.size() != C.store_count) {
+    lyap_set_error_message("no stored ADI shifts for this problem", __FILE__, __LINE__);
+    return LYAP_ERR_ARG;
+  }
+  const int ns = C.store_count;
+  // [W, V] and the weights of W
+  LYAP_TRY(ensure(C.adiW, (size_t)n * 2 * m * sizeof(T) + 64));
+  LYAP_TRY(ensure(C.adiY, (size_t)m * 8 + 64));
+  LYAP_TRY(ensure(C.adiG, (size_t)m * m * 8 + 64));
+  T* Y = P<T>(C.adiW);
+  double* y0 = P<double>(C.adiY);
+  LYAP_CUDA_TRY(cudaMemcpyAsync(Y, Z, sizeof(T) * (size_t)n * m, cudaMemcpyDeviceToDevice, C.s));
+  if (ldlt) LYAP_CUDA_TRY(cudaMemcpyAsync(y0, y, sizeof(double) * m, cudaMemcpyDeviceToDevice, C.s));
+  double* sc = P<double>(C.scal) + 48;
+  auto resnorm = [&](double* out) -> int {
+    // ||W diag(y0) W^T||_F^2 through the m x m Gram matrix of W (FP64; C.Lst is free here)
+    LYAP_TRY(ensure(C.Lst, (size_t)n * m * 8 + 64));
+    double* W64 = P<double>(C.Lst);
+    LYAP_TRY((copy_cast<T, double>(Y, n, m, n, W64, n, 1.0, C.s)));
+    LYAP_TRY(gemm<double>('T', 'N', m, m, n, 1.0, W64, n, W64, n, 0.0, P<double>(C.adiG), m, C.s));
+    adi_resnorm_kernel<<<1, 256, 0, C.s>>>(P<double>(C.adiG), m, ldlt ? y0 : nullptr, out);
+    LYAP_CUDA_TRY(cudaGetLastError());
+    lyap_count_launch();
+    return LYAP_OK;
+  };
+  mark(C, LYAP_PHASE_FACTOR);
+  LYAP_TRY(resnorm(sc));
+  double r0 = 0.0;
+  LYAP_TRY(sync_read(C, sc, &r0, sizeof(double)));
+  int c = 0;
+  for (int it = 0; it < ao.maxit && r0 > 0.0; ++it) {
+    const int j = it % ns;
+    const double p = C.adi_p[j];
+    if (c + m > 2 * n + 8) {
+      lyap_set_error_message("ADI factor exceeds its capacity", __FILE__, __LINE__);
+      return LYAP_ERR_CAPACITY;
+    }
+    mark(C, LYAP_PHASE_FACTOR);
+    // V = (A0 + p_j I)^{-1} W into the second half of Y
+    LYAP_TRY(factor_product<T>(C, n, m, o.prec, j, Y));
+    adi_step_kernel<T><<<nblk((int64_t)n * m), 256, 0, C.s>>>(Y, n, m, p, ldlt ? 1.0 : std::sqrt(-2.0 * p), Z, c, y0,
+                                                             ldlt ? y : nullptr);
+    LYAP_CUDA_TRY(cudaGetLastError());
+    lyap_count_launch();
+    c += m;
+    if ((double)c > o.rho * (double)n) {
+      mark(C, LYAP_PHASE_COMPRESS);
+      int r = 0;
+      if (!ldlt) {
+        LYAP_TRY(qrcp_truncate<T>(Z, n, c, n, o.rank_tol, C.qr, C.s));
+        LYAP_TRY(sync_read(C, C.qr.rank, &r, sizeof(int)));
+      } else {
+        LYAP_TRY(rank_trunc_ldlt<T>(C, Z, n, c, y, o.rank_tol, &r));
+      }
+      c = r;
+    }
+    mark(C, LYAP_PHASE_FACTOR);
+    LYAP_TRY(resnorm(sc));
+    double rj = 0.0;
+    LYAP_TRY(sync_read(C, sc, &rj, sizeof(double)));
+    if (!std::isfinite(rj)) return LYAP_ERR_NONFINITE;
+    if (std::sqrt(rj) <= ao.tol * std::sqrt(r0)) break;
+  }
+  mark(C, LYAP_PHASE_OTHER);
+  int qrs = 0, tcs = 0;
+  LYAP_TRY(sync_read(C, C.qr.status, &qrs, sizeof(int)));
+  if (qrs) return qrs;
+  if (s16) {
+    LYAP_TRY(tc_status_read(&tcs));
+    if (tcs) return tcs;
+  }
+  *c_out = c;
+  return LYAP_OK;
+}
+
 // Run the sign-Newton factor iteration on Z (working precision, n x c0 in C.Zw, column-major).
 // compute == true: compute and store the inverse sequence from the working
 // matrix in C.A0 (row-major, already scaled); else replay the stored sequence.
@@ -1151,6 +1368,9 @@ int lyap_opts_default(lyap_opts_t* o) {
   o->stag_theta = 0.9;
   o->stag_count = 2;
   o->project_psd = 1;
+  o->inner = LYAP_INNER_SIGN;
+  o->adi_shifts = 8;
+  o->adi_maxit = 200;
   return LYAP_OK;
 }
 
@@ -1192,7 +1412,7 @@ int lyap_ctx_destroy(lyap_ctx_t* C) {
                 &C->Lm, &C->Zs, &C->Zbest, &C->G, &C->gram, &C->ysol, &C->ybest, &C->ytmp, &C->Lw, &C->Sd,
                 &C->Vs, &C->Lst, &C->Rtau, &C->Bm, &C->VB, &C->qrBar, &C->qrStatus, &C->qrCand, &C->qrNorms, &C->qrPiv, &C->qrRdiag, &C->qrWork,
                 &C->qrRank, &C->eigWork32, &C->eigBig, &C->eigX, &C->eigR, &C->eigS, &C->eigHX, &C->eigE, &C->eigLam,
-                &C->eigRed, &C->eigW, &C->eigPv, &C->eigInt, &C->At, &C->Ct, &C->ZY, &C->adjT, &C->Hf, &C->tl, &C->inv1, &C->pnw};
+                &C->eigRed, &C->eigW, &C->eigPv, &C->eigInt, &C->At, &C->Ct, &C->ZY, &C->adjT, &C->Hf, &C->tl, &C->inv1, &C->pnw, &C->adiW, &C->adiY, &C->adiG};
   for (Buf* b : all) free_buf(*b);
   for (lyap_ctx* w : C->pool) lyap_ctx_destroy(w);
   for (cudaStream_t st : C->pool_streams) cudaStreamDestroy(st);
@@ -1352,6 +1572,7 @@ static int newton_solve(Ctx& C, const Problem& pb, const double* Lr, int mr, con
     // sequence of kmax inverses would exceed mem_budget
     int ce = o.ckpt_every > 0 ? o.ckpt_every : 0;
     if (ce == 0 && o.mem_budget > 0 && (double)no.kmax * (double)inv_bytes > (double)o.mem_budget) ce = 4;
+    if (o.inner == LYAP_INNER_ADI) ce = 0;  // the shifted inverses are always stored
     C.store_ckpt = ce;
     C.store_welt = sizeof(T);
     if (ce) {
@@ -1404,7 +1625,16 @@ static int newton_solve(Ctx& C, const Problem& pb, const double* Lr, int mr, con
     }
   }
   int c = 0;
-  LYAP_TRY(newton_run<T>(C, n, mr, ldlt, no, compute, &c, info));
+  const bool adi = (o.inner == LYAP_INNER_ADI);
+  if (adi) {
+    AdiOpts ao;
+    ao.shifts = o.adi_shifts > 0 ? o.adi_shifts : 8;
+    ao.maxit = o.adi_maxit > 0 ? o.adi_maxit : 200;
+    ao.tol = o.adi_tol > 0 ? o.adi_tol : std::max(10.0 * unit_roundoff(o.u_s), 1e-14);
+    LYAP_TRY(adi_run<T>(C, n, mr, ldlt, no, ao, compute, &c, info));
+  } else {
+    LYAP_TRY(newton_run<T>(C, n, mr, ldlt, no, compute, &c, info));
+  }
   if (iters) *iters = C.store_count;
   if (c > zcap_out) {
     *r_out = c;
@@ -1413,13 +1643,15 @@ static int newton_solve(Ctx& C, const Problem& pb, const double* Lr, int mr, con
   }
   // undo the prescaling: X = 2^-e0 X'  ->  Z = 2^{-e0/2} Z' (Cholesky, with the final 1/sqrt 2),
   // Y = 2^-e0 Y'/2 (LDL^T)
+  // (the ADI factor carries no final 1/sqrt 2 / 1/2: its iterates approximate X itself)
   const double e0 = (double)C.store_e0;
   if (!ldlt) {
-    LYAP_TRY((copy_cast<T, double>(P<T>(C.Zw), n, c, n, Zout, ldo, pow(2.0, -0.5 * e0) / sqrt(2.0), C.s)));
+    LYAP_TRY((copy_cast<T, double>(P<T>(C.Zw), n, c, n, Zout, ldo, pow(2.0, -0.5 * e0) / (adi ? 1.0 : sqrt(2.0)),
+                                   C.s)));
   } else {
     LYAP_TRY((copy_cast<T, double>(P<T>(C.Zw), n, c, n, Zout, ldo, 1.0, C.s)));
     LYAP_CUDA_TRY(cudaMemcpyAsync(yout, C.yv.p, sizeof(double) * c, cudaMemcpyDeviceToDevice, C.s));
-    scale_vec_kernel<<<1, 256, 0, C.s>>>(yout, c, 0.5 * pow(2.0, -e0));
+    scale_vec_kernel<<<1, 256, 0, C.s>>>(yout, c, (adi ? 1.0 : 0.5) * pow(2.0, -e0));
     lyap_count_launch();
   }
   *r_out = c;
@@ -1657,6 +1889,7 @@ static int check_problem(const Problem& pb, const lyap_opts_t* o, double* Z, int
   if (pb.n <= 0 || pb.m <= 0 || pb.lda < pb.n || pb.ldl < pb.n || ldz < pb.n || z_cap <= 0) return LYAP_ERR_ARG;
   if (pb.S && pb.lds < pb.m) return LYAP_ERR_ARG;
   if (o->u_s < 0 || o->u_s > 3 || o->scaling < 0 || o->scaling > 4 || o->kmax <= 0 || o->imax < 0) return LYAP_ERR_ARG;
+  if (o->inner != LYAP_INNER_SIGN && o->inner != LYAP_INNER_ADI) return LYAP_ERR_ARG;
   if (o->u != LYAP_FP64 || o->u_r != LYAP_FP64 || o->u_c != LYAP_FP64) {
     lyap_set_error_message("only u = u_r = u_c = LYAP_FP64 is implemented", __FILE__, __LINE__);
     return LYAP_ERR_ARG;

@@ -234,3 +234,19 @@ def test_adjoint_n2048_normal_blocks_checkpointed_and_central_differences():
         fd = (loss(A, L + h * T(F)) - loss(A, L - h * T(F))) / (2 * h)
         an = float(np.sum(dL * F))
         assert abs(fd - an) <= 1e-6 * abs(an), (k, fd, an)
+
+
+def test_adjoint_with_adi_inner_matches_oracle():
+    # the adjoint replays the stored shifted inverses transposed ((A + p I)^{-T} = (A^T + p I)^{-1})
+    lp = lib()
+    d = gen.paper_synthetic(64, 1.0)
+    A, L = d["A"], d["L"]
+    Cm = gen.rng(gen.SEED_BASE + 50).standard_normal((3, 64))
+    o = lp.make_opts(u_s="fp16", inner="adi", tau_ir=1e-13, imax=30)
+    Z, _, info = lp.solve_ir(T(A), T(L), opts=o)
+    assert info.converged
+    out = lp.adjoint(T(A), T(L), Z, T(Cm), opts=o)
+    assert out["info"].converged
+    ref = O.adjoint(A, L, Cm)
+    assert relF(N(out["dA"]), ref["dA"]) <= 1e-9
+    assert relF(N(out["dL"]), ref["dL"]) <= 1e-9

@@ -346,3 +346,52 @@ def test_sign_solve_norm2_and_spectral_scaling(scaling):
     assert info2.converged, info2.as_dict()
     assert rel(N(Z2) @ N(Z2).T, X) <= 1e-10
     assert O.residual_eq41(A, N(Z2), W) <= 1e-12
+
+
+# ------------------------------------------------ low-rank ADI as the inner solver
+
+def test_adi_single_solve_fp64_matches_bartels_stewart():
+    # lyap_sign_solve with inner = ADI at FP64: one low-rank ADI solve to ||W W^T|| <= 1e-14
+    d = gen.convdiff_shifted(grid=10, m=2)
+    A, L = d["A"], d["L"]
+    X = O.bartels_stewart(A, L @ L.T)
+    Z, _, info = lib().sign_solve(T(A), T(L), u_s="fp64", inner="adi", adi_shifts=10, rho=0.5)
+    assert rel(N(Z) @ N(Z).T, X) <= 1e-10
+    # the shifts are recorded in info.mu: negative and ascending (largest magnitude first)
+    p = np.array(list(info.mu)[:10])
+    assert np.all(p < 0) and np.all(np.diff(p) > 0)
+
+
+@pytest.mark.parametrize("u_s", ["fp16", "fp32"])
+def test_ir_chol_adi_inner_matches_oracle(u_s):
+    # IR-Chol with low-rank ADI inner solves (16-bit / FP32 shifted inverses, stored once and
+    # reused by every correction): the FP64 refinement reaches 1e-12 and the Bartels-Stewart
+    # solution, as the oracle's IR with its ADI solver does on the same input
+    d = gen.convdiff_shifted(grid=20, m=3)
+    A, L = d["A"], d["L"]
+    W = L @ L.T
+    X = O.bartels_stewart(A, W)
+    Z, _, info = lib().solve_ir(T(A), T(L), u_s=u_s, inner="adi", tau_ir=1e-12, imax=30)
+    assert info.converged, info.as_dict()
+    assert rel(N(Z) @ N(Z).T, X) <= 1e-10
+    assert O.residual_eq41(A, N(Z), W) <= 1e-12
+    assert info.n_inversions == 8                      # the shifted inverses, computed once
+    Zo, io = O.ir_chol(A, L, O.Opts(u_s=u_s, inner="adi", tau_ir=1e-12, imax=30))
+    assert io.converged
+    # the GPU's shifted inverses are 16-bit operands with FP32 accumulation, the oracle rounds
+    # every matrix result to u_s: the GPU contracts at least as fast (3 against 7 steps at FP16)
+    assert info.ir_steps <= io.ir_steps + 1, (info.ir_steps, io.ir_steps)
+
+
+def test_ir_ldlt_adi_inner_indefinite():
+    # IR-LDLT with ADI inner solves on the Sec. 4.2 family (symmetric A, real spectrum) with
+    # an indefinite S: against the Bartels-Stewart solution of the indefinite equation
+    d = gen.paper_synthetic(120, 1.0)
+    A, L = d["A"], d["L"]
+    S = np.diag([1.0, -1.0, 1.0])
+    W = L @ S @ L.T
+    X = O.bartels_stewart(A, W)
+    Z, D, info = lib().solve_ir(T(A), T(L), S=T(S), u_s="fp16", inner="adi", tau_ir=1e-12, imax=30)
+    assert info.converged, info.as_dict()
+    assert rel((N(Z) * N(D)) @ N(Z).T, X) <= 1e-10
+    assert O.residual_eq41(A, N(Z), W, N(D)) <= 1e-12
