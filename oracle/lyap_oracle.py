@@ -67,6 +67,9 @@ def rnd(x, prec: str):
 class Opts:
     """Algorithm parameters; defaults are the paper's (Sec. 4.1)."""
     u_s: str = "fp64"              # solver precision (Algorithms IR-Chol / IR-LDLT)
+    u: str = "fp64"                # working precision = u_r = u_c (Table 2.1: fp64 or fp32); the
+                                   # residual factors and the updated solution factor are
+                                   # stored (rounded) in u
     scaling: str = "frob"          # "frob" (Sec. 4, chosen), "det", "norm2", "spectral", "none"
                                    # (the scalings listed in Sec. 3.1)
     tau_newton: float = 0.0        # <= 0: 10 sqrt(n u_s)  (Eq. (3.4))
@@ -542,8 +545,8 @@ def ir_chol(A, L, opts: Opts):
     Returns (Z, IRInfo).
     """
     n = A.shape[0]
-    tau_ir = opts.tau_ir if opts.tau_ir > 0 else n * UNIT["fp64"]
-    eta_s = opts.eta_s if opts.eta_s > 0 else 10.0 * UNIT["fp64"]
+    tau_ir = opts.tau_ir if opts.tau_ir > 0 else n * UNIT[opts.u]
+    eta_s = opts.eta_s if opts.eta_s > 0 else 10.0 * UNIT[opts.u]
     info = IRInfo()
     if opts.inner == "adi":
         def solve(Lr, r):
@@ -552,6 +555,7 @@ def ir_chol(A, L, opts: Opts):
         def solve(Lr, r):
             return newton_chol(A, Lr, opts, r)
     Z, rec = solve(L, None)
+    Z = rnd(Z, opts.u)
     K = len(rec.inverses)
     info.n_inversions = K
     info.newton_calls, info.newton_total, info.newton_max = 1, K, K
@@ -579,12 +583,12 @@ def ir_chol(A, L, opts: Opts):
             break
         if i == opts.imax + 1:
             break
-        Lp, Lm = rnd(Lp, opts.u_s), rnd(Lm, opts.u_s)
+        Lp, Lm = rnd(rnd(Lp, opts.u), opts.u_s), rnd(rnd(Lm, opts.u), opts.u_s)
         Zp = solve(Lp, rec)[0] if Lp.shape[1] else np.zeros((n, 0))
         Zm = solve(Lm, rec)[0] if Lm.shape[1] else np.zeros((n, 0))
         info.newton_calls += 1
         info.newton_total += K
-        Z = sol_upt_chol(Z, Zp, Zm, eta_s)
+        Z = rnd(sol_upt_chol(Z, Zp, Zm, eta_s), opts.u)
         info.ir_steps = i
     info.res_final = best[0]
     info.rank = best[1].shape[1]
@@ -605,8 +609,8 @@ def ir_ldlt(A, L, S, opts: Opts):
     s, Vs = np.linalg.eigh(np.asarray(S, dtype=np.float64))
     L = L @ Vs
     project = opts.project_psd and bool(np.all(s >= 0))
-    tau_ir = opts.tau_ir if opts.tau_ir > 0 else n * UNIT["fp64"]
-    eta_s = opts.eta_s if opts.eta_s > 0 else 10.0 * UNIT["fp64"]
+    tau_ir = opts.tau_ir if opts.tau_ir > 0 else n * UNIT[opts.u]
+    eta_s = opts.eta_s if opts.eta_s > 0 else 10.0 * UNIT[opts.u]
     info = IRInfo()
     if opts.inner == "adi":
         def solve(Lr, yr, r):
@@ -616,6 +620,7 @@ def ir_ldlt(A, L, S, opts: Opts):
         def solve(Lr, yr, r):
             return newton_ldlt(A, Lr, yr, opts, r)
     Z, y, rec = solve(L, s, None)
+    Z, y = rnd(Z, opts.u), rnd(y, opts.u)
     K = len(rec.inverses)
     info.n_inversions = K
     info.newton_calls, info.newton_total, info.newton_max = 1, K, K
@@ -643,11 +648,12 @@ def ir_ldlt(A, L, S, opts: Opts):
             break
         if i == opts.imax + 1:
             break
-        Ld, sd = rnd(Ld, opts.u_s), rnd(sd, opts.u_s)
+        Ld, sd = rnd(rnd(Ld, opts.u), opts.u_s), rnd(rnd(sd, opts.u), opts.u_s)
         Zd, yd, _ = solve(Ld, sd, rec)
         info.newton_calls += 1
         info.newton_total += K
         Z, y = sol_upt_ldlt(Z, y, Zd, yd, eta_s, project)
+        Z, y = rnd(Z, opts.u), rnd(y, opts.u)
         info.ir_steps = i
     info.res_final = best[0]
     info.rank = best[1].shape[1]

@@ -580,3 +580,20 @@ def test_lr_adi_residual_identity_and_ir():
     Zi, info = O.ir_chol(A, L, O.Opts(u_s="fp16", inner="adi", tau_ir=1e-13))
     assert info.converged
     assert rel(Zi @ Zi.T, X) <= 1e-10
+
+
+def test_ir_working_precision_fp32_limits_the_residual():
+    # Table 2.1 (u = fp32 rows): with the residual factors and the solution factor stored in
+    # FP32 the refinement reaches the default tau = n u (u = 2^-24) and stalls near u; with
+    # u = fp64 the same refinement goes on to FP64 level
+    d = gen.paper_synthetic(100, 1.0)
+    A, L = d["A"], d["L"]
+    Z, info = O.ir_chol(A, L, O.Opts(u_s="fp16", u="fp32"))
+    assert info.converged and info.res_final <= 100 * 2.0 ** -24
+    _, forced = O.ir_chol(A, L, O.Opts(u_s="fp16", u="fp32", tau_ir=1e-30, imax=12))
+    assert forced.stagnated and 1e-10 < forced.res_final < 100 * 2.0 ** -24
+    _, f64 = O.ir_chol(A, L, O.Opts(u_s="fp16", u="fp64", tau_ir=1e-30, imax=12))
+    assert f64.res_final < 1e-14
+    s = np.array([1.0, -1.0, 1.0])
+    _, _, fl = O.ir_ldlt(A, L, np.diag(s), O.Opts(u_s="fp16", u="fp32", tau_ir=1e-30, imax=12))
+    assert 1e-10 < fl.res_final < 100 * 2.0 ** -24
