@@ -102,9 +102,13 @@ typedef struct {
                            on the FP16 tensor cores above a size threshold), 1 = FP64 SIMT,
                            2 = always emulated (see lyap_dgemm) */
   int u, u_r, u_c;      /* lyap_prec_t of the working precision, of the residual and of the
-                           solution update (Algorithms IR-Chol / IR-LDLT, Table 2.1): this
-                           library implements u = u_r = u_c = LYAP_FP64 (the configuration the
-                           analysis of Sec. 2 targets); any other value returns LYAP_ERR_ARG */
+                           solution update (Algorithms IR-Chol / IR-LDLT, Table 2.1): the
+                           presets u = u_r = u_c = LYAP_FP64 (default) or LYAP_FP32; other
+                           combinations return LYAP_ERR_ARG.  With FP32 the residual factors
+                           and the updated solution factor are stored rounded to FP32 (their
+                           products run in FP64), tau_ir and eta_s default to n u and 10 u of
+                           FP32, and the attainable residual is near u = 2^-24 (Table 2.1's
+                           u = fp32 rows).  The adjoint accepts FP64 only */
   int inner;            /* lyap_inner_t: inner solver of the refinement (and of lyap_sign_solve) */
   int adi_shifts;       /* low-rank ADI: number of cyclic real shifts (<= 0: 8; at most kmax) */
   int adi_maxit;        /* low-rank ADI: step limit per solve (<= 0: 200) */

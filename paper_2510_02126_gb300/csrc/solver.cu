@@ -1890,8 +1890,8 @@ static int check_problem(const Problem& pb, const lyap_opts_t* o, double* Z, int
   if (pb.S && pb.lds < pb.m) return LYAP_ERR_ARG;
   if (o->u_s < 0 || o->u_s > 3 || o->scaling < 0 || o->scaling > 4 || o->kmax <= 0 || o->imax < 0) return LYAP_ERR_ARG;
   if (o->inner != LYAP_INNER_SIGN && o->inner != LYAP_INNER_ADI) return LYAP_ERR_ARG;
-  if (o->u != LYAP_FP64 || o->u_r != LYAP_FP64 || o->u_c != LYAP_FP64) {
-    lyap_set_error_message("only u = u_r = u_c = LYAP_FP64 is implemented", __FILE__, __LINE__);
+  if (o->u != o->u_r || o->u != o->u_c || (o->u != LYAP_FP64 && o->u != LYAP_FP32)) {
+    lyap_set_error_message("u = u_r = u_c must be LYAP_FP64 or LYAP_FP32", __FILE__, __LINE__);
     return LYAP_ERR_ARG;
   }
   return LYAP_OK;
@@ -1947,8 +1947,15 @@ static int solve_common(Ctx& C, const Problem& pb, const lyap_opts_t& o, bool re
     LYAP_CUDA_TRY(cudaMemcpyAsync(sc + 22, h, sizeof(double), cudaMemcpyHostToDevice, C.s));
     LYAP_CUDA_TRY(cudaStreamSynchronize(C.s));
   }
-  const double tau_ir = o.tau_ir > 0 ? o.tau_ir : (double)n * unit_roundoff(LYAP_FP64);
-  const double eta_s = o.eta_s > 0 ? o.eta_s : 10.0 * unit_roundoff(LYAP_FP64);
+  // working precision u = u_r = u_c (Table 2.1): the residual factors and the updated solution
+  // factor are stored in it (rounded when it is FP32; the products themselves run in FP64)
+  const int wu = o.u;
+  double* rscr = P<double>(C.part) + 4 * RED_BLOCKS;
+  auto to_u = [&](double* x, int64_t rows, int64_t cols) { return round_to_prec(x, rows, cols, rows, wu, rscr, C.s); };
+  LYAP_TRY(to_u(P<double>(C.Zs), n, c));
+  if (ldlt) LYAP_TRY(to_u(P<double>(C.ysol), c, 1));
+  const double tau_ir = o.tau_ir > 0 ? o.tau_ir : (double)n * unit_roundoff(wu);
+  const double eta_s = o.eta_s > 0 ? o.eta_s : 10.0 * unit_roundoff(wu);
   const bool project = (o.project_psd != 0) && !indefinite;
   double best = 1e300;
   int best_c = 0;
@@ -2006,6 +2013,7 @@ static int solve_common(Ctx& C, const Problem& pb, const lyap_opts_t& o, bool re
       double* Lpm = P<double>(C.Vs);
       LYAP_TRY((copy_cast<double, double>(P<double>(C.Lp), n, rp, n, Lpm, n, 1.0, C.s)));
       LYAP_TRY((copy_cast<double, double>(P<double>(C.Lm), n, rm, n, Lpm + (size_t)n * rp, n, 1.0, C.s)));
+      LYAP_TRY(to_u(Lpm, n, rp + rm));
       LYAP_TRY(newton_solve_any(C, pb, Lpm, rp, nullptr, false, o, false, G + (size_t)n * c, n, 2 * n, nullptr, &cp,
                                 nullptr, &it2));
       LYAP_TRY(newton_solve_any(C, pb, Lpm + (size_t)n * rp, rm, nullptr, false, o, false, G + (size_t)n * (c + cp), n,
@@ -2015,6 +2023,7 @@ static int solve_common(Ctx& C, const Problem& pb, const lyap_opts_t& o, bool re
       int rnew = 0;
       LYAP_TRY(sol_upt(C, n, c + cp + cm, c + cp, nullptr, true, eta_s, res_next, P<double>(C.Zs), nullptr, &rnew));
       c = rnew;
+      LYAP_TRY(to_u(P<double>(C.Zs), n, c));
     } else {
       LYAP_TRY(ensure(C.Vs, (size_t)n * (rp + 1) * 8 + 64));
       double* Ld = P<double>(C.Vs);
@@ -2025,6 +2034,8 @@ static int solve_common(Ctx& C, const Problem& pb, const lyap_opts_t& o, bool re
       LYAP_CUDA_TRY(cudaMemcpyAsync(ups, C.ysol.p, sizeof(double) * c, cudaMemcpyDeviceToDevice, C.s));
       double* sdel = ups + c + 2 * n + 8;
       LYAP_CUDA_TRY(cudaMemcpyAsync(sdel, C.Lm.p, sizeof(double) * rp, cudaMemcpyDeviceToDevice, C.s));
+      LYAP_TRY(to_u(Ld, n, rp));
+      LYAP_TRY(to_u(sdel, rp, 1));
       LYAP_TRY(round_to_prec(sdel, rp, 1, rp, o.u_s, P<double>(C.part) + 4 * RED_BLOCKS, C.s));
       LYAP_TRY(newton_solve_any(C, pb, Ld, rp, sdel, true, o, false, G + (size_t)n * c, n, 2 * n, ups + c, &cp, nullptr,
                                 &it2));
@@ -2033,6 +2044,8 @@ static int solve_common(Ctx& C, const Problem& pb, const lyap_opts_t& o, bool re
       int rnew = 0;
       LYAP_TRY(sol_upt(C, n, c + cp, c + cp, ups, project, eta_s, res_next, P<double>(C.Zs), P<double>(C.ysol), &rnew));
       c = rnew;
+      LYAP_TRY(to_u(P<double>(C.Zs), n, c));
+      LYAP_TRY(to_u(P<double>(C.ysol), c, 1));
     }
     info->ir_steps = i;
     if (c > n) c = n;

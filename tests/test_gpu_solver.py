@@ -191,14 +191,43 @@ def test_capacity_error():
     assert getattr(ei.value, "status", None) == lib().ERR_CAPACITY
 
 
-def test_working_precisions_other_than_fp64_rejected():
-    # u = u_r = u_c = FP64 is the implemented configuration (Table 2.1, bottom half)
+def test_mixed_working_precisions_rejected():
+    # the presets are u = u_r = u_c = FP64 or FP32 (Table 2.1); mixed settings and 16-bit
+    # working precisions are rejected
     d = gen.convdiff_shifted(grid=5, m=2)
     for field in ("u", "u_r", "u_c"):
         o = lib().make_opts("fp16", **{field: lib().FP32})
         with pytest.raises(Exception) as ei:
             lib().solve_ir(T(d["A"]), T(d["L"]), opts=o)
         assert getattr(ei.value, "status", None) == lib().ERR_ARG
+    o = lib().make_opts("fp16", u=lib().FP16, u_r=lib().FP16, u_c=lib().FP16)
+    with pytest.raises(Exception) as ei:
+        lib().solve_ir(T(d["A"]), T(d["L"]), opts=o)
+    assert getattr(ei.value, "status", None) == lib().ERR_ARG
+
+
+@pytest.mark.parametrize("form", ["chol", "ldlt"])
+def test_working_precision_fp32_preset(form):
+    # u = u_r = u_c = FP32 (Table 2.1, top half): the refinement reaches tau = n u of FP32 and,
+    # pushed further, stalls near u, as the oracle with the same storage points does; the
+    # FP64 preset goes on to FP64 level on the same input
+    d = gen.paper_synthetic(100, 1.0)
+    A, L = d["A"], d["L"]
+    S = np.diag([1.0, -1.0, 1.0]) if form == "ldlt" else None
+    Sg = T(S) if S is not None else None
+    f32 = dict(u=lib().FP32, u_r=lib().FP32, u_c=lib().FP32)
+    _, _, info = lib().solve_ir(T(A), T(L), S=Sg, opts=lib().make_opts("fp16", **f32))
+    assert info.converged and info.res_final <= 100 * 2.0 ** -24, info.as_dict()
+    _, _, forced = lib().solve_ir(T(A), T(L), S=Sg, opts=lib().make_opts("fp16", tau_ir=1e-30, imax=12, **f32))
+    assert forced.status == lib().WARN_STAGNATED
+    assert 1e-10 < forced.res_final < 100 * 2.0 ** -24, forced.as_dict()
+    if form == "chol":
+        _, ref = O.ir_chol(A, L, O.Opts(u_s="fp16", u="fp32", tau_ir=1e-30, imax=12))
+    else:
+        _, _, ref = O.ir_ldlt(A, L, S, O.Opts(u_s="fp16", u="fp32", tau_ir=1e-30, imax=12))
+    assert ref.res_final / 30 <= forced.res_final <= 30 * ref.res_final, (forced.res_final, ref.res_final)
+    _, _, f64 = lib().solve_ir(T(A), T(L), S=Sg, opts=lib().make_opts("fp16", tau_ir=1e-30, imax=12))
+    assert f64.res_final < 1e-14
 
 
 def test_nonfinite_input():
