@@ -1,6 +1,6 @@
 """Solver-level parity of the CUDA path (C ABI) with the CPU oracle: the
 sign-Newton solver (Algorithms Newton-Chol / Newton-LDLT) and the mixed-precision
-IR algorithms, judged on the exact solution (Schur method), the relative residual
+IR algorithms, checked against the exact solution (Schur method), the relative residual
 of Eq. (4.1), and the iteration counts that depend on A only."""
 import json
 import os
