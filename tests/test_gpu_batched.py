@@ -75,3 +75,25 @@ def test_batched_on_fresh_contexts_after_destroyed_ones():
         if lp._ctx is not None:
             lp._ctx.close()
             lp._ctx = None
+
+
+def test_batched_full_config_256():
+    # the batched workload at full size: 256 equations, n log-uniform in [64, 1024], rank 1..8,
+    # FP16 inner solves, FP64 refinement to 1e-12 (imax = 10, as the bench).  Every equation
+    # converges (residual of Eq. (4.1) from the factors); a seeded sample of 16 equals the lone
+    # lyap_solve_ir result and the oracle's Bartels-Stewart solution
+    lp = lib()
+    eqs = gen.batch_uneven(count=256, nmin=64, nmax=1024, rmax=8)
+    o = lp.make_opts(u_s="fp16", tau_ir=1e-12, imax=10)
+    Zs, infos, st = lp.solve_ir_batched([T(e["A"]) for e in eqs], [T(e["L"]) for e in eqs], opts=o, workers=8)
+    assert st == 0
+    assert all(inf.converged for inf in infos)
+    assert max(inf.res_final for inf in infos) <= 1e-12
+    for k in gen.rng(gen.SEED_BASE + 52).choice(256, size=16, replace=False):
+        e, Z = eqs[k], Zs[k]
+        X = N(Z) @ N(Z).T
+        Z1, _, inf1 = lp.solve_ir(T(e["A"]), T(e["L"]), opts=o)
+        X1 = N(Z1) @ N(Z1).T
+        assert np.linalg.norm(X - X1) <= 1e-10 * np.linalg.norm(X1), k
+        Xo = O.bartels_stewart(e["A"], e["L"] @ e["L"].T)
+        assert np.linalg.norm(X - Xo) <= 1e-10 * np.linalg.norm(Xo), k
