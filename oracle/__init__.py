@@ -28,6 +28,8 @@ Functions and the passages they follow:
 * ``lr_adi_chol``/``lr_adi_ldlt``/``adi_record`` -- low-rank ADI with real cyclic shifts as
   the alternative inner solver (Sec. 5 names ADI-based solvers inside the same refinement
   framework; ``Opts.inner = "adi"`` in ``ir_chol``/``ir_ldlt``)
+* ``eksm_chol``/``eksm_ldlt`` -- the extended Krylov (Galerkin) method as the Krylov
+  alternative inner solver (``Opts.inner = "eksm"``)
 * ``sign_block``/``sign_matrix``/``frechet_sign``/``kappa_sign_fro`` -- sign(B) of
   B = [[A, W], [0, -A^T]], its Frechet derivative and kappa_sign(B) in the Frobenius norm,
   the indicator Sec. 4.2 uses to explain the accuracy of the Newton solver

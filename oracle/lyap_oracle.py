@@ -18,6 +18,7 @@ __all__ = [
     "ir_chol", "ir_ldlt", "residual_eq41", "adjoint", "norm_xyx", "lyap_operator_kappa2_normal",
     "sign_block", "sign_matrix", "frechet_sign", "kappa_sign_fro",
     "ADIRecord", "adi_shifts", "adi_record", "lr_adi_chol", "lr_adi_ldlt",
+    "EKSMRecord", "eksm_chol", "eksm_ldlt",
 ]
 
 # Unit roundoffs of Table 1.1 (t significand bits incl. the implicit bit: u = 2^-t).
@@ -90,11 +91,12 @@ class Opts:
     stag_theta: float = 0.9        # Eq. (4.2)
     stag_count: int = 2
     project_psd: bool = True       # SolUpt projection onto the PSD cone (Sec. 2.1)
-    inner: str = "sign"            # inner solver: "sign" (Sec. 3) or "adi" (low-rank ADI, the
-                                   # alternative Sec. 5 names; real shifts, see lr_adi_*)
+    inner: str = "sign"            # inner solver: "sign" (Sec. 3), "adi" (low-rank ADI) or "eksm"
+                                   # (extended Krylov): the alternatives Sec. 5 names
     adi_shifts: int = 8            # number of cyclic real shifts
     adi_tol: float = 0.0           # <= 0: max(10 u_s, 1e-14); ||W S W^T||_F <= tol ||L S L^T||_F
     adi_maxit: int = 200
+    eksm_maxit: int = 60           # extended Krylov: block steps per solve (tolerance: adi_tol)
 
 
 def _u(prec: str) -> float:
@@ -419,6 +421,79 @@ def lr_adi_ldlt(A, L, y, opts: Opts, rec: ADIRecord | None = None):
 
 
 # ---------------------------------------------------------------------------
+# Extended Krylov subspace method as the inner solver (the Krylov alternative Sec. 5 names):
+# Galerkin projection onto span{L, A^-1 L, A L, A^-2 L, A^2 L, ...}
+# ---------------------------------------------------------------------------
+@dataclass
+class EKSMRecord:
+    """A^{-1} rounded to u_s (depends on A only: every correction solve reuses it)."""
+    inverses: list = field(default_factory=list)
+
+
+def _orth(W):
+    Q, _ = np.linalg.qr(W)
+    return Q
+
+
+def _eksm(A, L, y, opts: Opts, rec: EKSMRecord | None, ldlt: bool):
+    """Block extended Krylov (Galerkin).  U_1 = orth([L, A^{-1} L]); step j takes the two
+    halves of the newest block U_j to [A U_j^(1), A^{-1} U_j^(2)], orthogonalises it against
+    V_j = [U_1, ..., U_j] (twice) into U_{j+1}.  With T_j = V_j^T A V_j and E = V_j^T L,
+    T_j Y + Y T_j^T + E diag(y) E^T = 0 (Bartels-Stewart, FP64) gives X_j = V_j Y V_j^T, whose
+    residual has norm sqrt(2) ||U_{j+1}^T A V_j Y||_F (A V_j lies in span V_{j+1}); the
+    iteration stops when that is <= tol ||L diag(y) L^T||_F.  Products and the basis are
+    rounded to u_s.  Returns (Z, yZ, rec, steps, resnorm) with X_j = Z diag(yZ) Z^T
+    (Cholesky type: the eigenvalues of Y below zero are dropped, yZ = 1)."""
+    n, m = L.shape
+    p_ = opts.u_s
+    if rec is None:
+        rec = EKSMRecord(inverses=[rnd(np.linalg.inv(rnd(A, p_)), p_)])
+    Ai = rec.inverses[0]
+    tol = opts.adi_tol if opts.adi_tol > 0 else max(10.0 * _u(p_), 1e-14)
+    y0 = np.ones(m) if y is None else np.asarray(y, dtype=np.float64)
+    Lr = rnd(L, p_)
+    nrm0 = np.linalg.norm((Lr * y0) @ Lr.T, "fro")
+    V = rnd(_orth(np.hstack([Lr, rnd(Ai @ Lr, p_)])), p_)
+    U = V
+    Y = np.zeros((V.shape[1], V.shape[1]))
+    Vy = V
+    steps, res = 0, math.inf
+    for j in range(opts.eksm_maxit):
+        W = rnd(np.hstack([A @ U[:, :m], Ai @ U[:, m:]]), p_)
+        for _ in range(2):
+            W = W - V @ (V.T @ W)
+        Un = rnd(_orth(W), p_)
+        AV = A @ V
+        T = V.T @ AV
+        E = V.T @ Lr
+        Y = bartels_stewart(T, (E * y0) @ E.T)
+        Vy = V
+        steps = j + 1
+        res = math.sqrt(2.0) * np.linalg.norm((Un.T @ AV) @ Y, "fro")
+        if nrm0 == 0.0 or res <= tol * nrm0 or V.shape[1] + Un.shape[1] > n:
+            break
+        V = np.hstack([V, Un])
+        U = Un
+    lam, Q = np.linalg.eigh((Y + Y.T) / 2)
+    if ldlt:
+        keep = np.abs(lam) > 1e-14 * max(np.max(np.abs(lam)), 1e-300)
+        return rnd(Vy @ Q[:, keep], p_), lam[keep], rec, steps, res
+    keep = lam > 1e-14 * max(np.max(lam), 1e-300)
+    return rnd(Vy @ (Q[:, keep] * np.sqrt(lam[keep])), p_), np.ones(int(keep.sum())), rec, steps, res
+
+
+def eksm_chol(A, L, opts: Opts, rec: EKSMRecord | None = None):
+    """Extended Krylov for A X + X A^T + L L^T = 0: returns (Z, rec, steps, resnorm)."""
+    Z, _, rec, steps, res = _eksm(A, L, None, opts, rec, False)
+    return Z, rec, steps, res
+
+
+def eksm_ldlt(A, L, y, opts: Opts, rec: EKSMRecord | None = None):
+    """Extended Krylov for A X + X A^T + L diag(y) L^T = 0: returns (Z, yZ, rec, steps, resnorm)."""
+    return _eksm(A, L, y, opts, rec, True)
+
+
+# ---------------------------------------------------------------------------
 # Residual factorisation and solution update, Sec. 2
 # ---------------------------------------------------------------------------
 
@@ -551,6 +626,9 @@ def ir_chol(A, L, opts: Opts):
     if opts.inner == "adi":
         def solve(Lr, r):
             return lr_adi_chol(A, Lr, opts, r)[:2]
+    elif opts.inner == "eksm":
+        def solve(Lr, r):
+            return eksm_chol(A, Lr, opts, r)[:2]
     else:
         def solve(Lr, r):
             return newton_chol(A, Lr, opts, r)
@@ -615,6 +693,10 @@ def ir_ldlt(A, L, S, opts: Opts):
     if opts.inner == "adi":
         def solve(Lr, yr, r):
             Zr, yZ, r2, _, _ = lr_adi_ldlt(A, Lr, yr, opts, r)
+            return Zr, yZ, r2
+    elif opts.inner == "eksm":
+        def solve(Lr, yr, r):
+            Zr, yZ, r2, _, _ = eksm_ldlt(A, Lr, yr, opts, r)
             return Zr, yZ, r2
     else:
         def solve(Lr, yr, r):

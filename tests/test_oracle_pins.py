@@ -597,3 +597,49 @@ def test_ir_working_precision_fp32_limits_the_residual():
     s = np.array([1.0, -1.0, 1.0])
     _, _, fl = O.ir_ldlt(A, L, np.diag(s), O.Opts(u_s="fp16", u="fp32", tau_ir=1e-30, imax=12))
     assert 1e-10 < fl.res_final < 100 * 2.0 ** -24
+
+
+# ----------------------------------------------------------- extended Krylov (inner solver)
+
+def test_eksm_residual_formula_and_exactness():
+    # the Galerkin residual norm sqrt(2) ||U_{j+1}^T A V_j Y||_F equals the explicit residual
+    # (A V_j lies in span V_{j+1}); once the space is all of R^n the projection is exact
+    d = gen.convdiff_shifted(grid=8, m=2)
+    A, L = d["A"], d["L"]
+    W = L @ L.T
+    for steps in (2, 4):
+        Z, _, st, res = O.eksm_chol(A, L, O.Opts(u_s="fp64", eksm_maxit=steps, adi_tol=1e-300))
+        Xk = Z @ Z.T
+        R = A @ Xk + Xk @ A.T + W
+        assert st == steps and abs(res - np.linalg.norm(R)) <= 1e-9 * np.linalg.norm(R)
+    # the space after 3 steps is span{L, A^-1 L, A L, A^-2 L, A^2 L, A^-3 L} (the block
+    # powers written out and orthonormalised at once), and X_3 is the Galerkin solution on
+    # it (the projected equation solved by the library's Lyapunov routine)
+    Ai = np.linalg.inv(A)
+    K = np.hstack([L, Ai @ L, A @ L, Ai @ Ai @ L, A @ A @ L, Ai @ Ai @ Ai @ L])
+    Vk, _ = np.linalg.qr(K)
+    s = np.array([1.0, -1.0])
+    for y in (None, s):
+        ys = np.ones(2) if y is None else y
+        Tk = Vk.T @ A @ Vk
+        Ek = Vk.T @ L
+        Yk = sla.solve_continuous_lyapunov(Tk, -(Ek * ys) @ Ek.T)
+        Xref = Vk @ Yk @ Vk.T
+        if y is None:
+            Z, _, _, _ = O.eksm_chol(A, L, O.Opts(u_s="fp64", eksm_maxit=3, adi_tol=1e-300))
+            assert rel(Z @ Z.T, Xref) <= 1e-9
+        else:
+            Zl, yl, _, _, _ = O.eksm_ldlt(A, L, y, O.Opts(u_s="fp64", eksm_maxit=3, adi_tol=1e-300))
+            assert rel((Zl * yl) @ Zl.T, Xref) <= 1e-9
+
+
+def test_ir_with_eksm_inner_converges():
+    d = gen.convdiff_shifted(grid=8, m=2)
+    A, L = d["A"], d["L"]
+    Z, info = O.ir_chol(A, L, O.Opts(u_s="fp16", inner="eksm", tau_ir=1e-13))
+    assert info.converged and rel(Z @ Z.T, O.bartels_stewart(A, L @ L.T)) <= 1e-10
+    d = gen.paper_synthetic(60, 1.0)
+    S = np.diag([1.0, -1.0, 1.0])
+    Zl, yl, il = O.ir_ldlt(d["A"], d["L"], S, O.Opts(u_s="fp16", inner="eksm", tau_ir=1e-13))
+    assert il.converged
+    assert rel((Zl * yl) @ Zl.T, O.bartels_stewart(d["A"], d["L"] @ S @ d["L"].T)) <= 1e-10
