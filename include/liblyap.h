@@ -112,8 +112,10 @@ typedef struct {
   int inner;            /* lyap_inner_t: inner solver of the refinement (and of lyap_sign_solve) */
   int adi_shifts;       /* low-rank ADI: number of cyclic real shifts (<= 0: 8; at most kmax) */
   int adi_maxit;        /* low-rank ADI: step limit per solve (<= 0: 200) */
-  double adi_tol;       /* low-rank ADI: stop once ||W_j S W_j^T||_F <= adi_tol ||L S L^T||_F
-                           (<= 0: max(10 u_s, 1e-14)) */
+  double adi_tol;       /* low-rank ADI and extended Krylov: stop once the residual of the inner
+                           solve is <= adi_tol ||L S L^T||_F (<= 0: max(10 u_s, 1e-14)) */
+  int eksm_maxit;       /* extended Krylov: block steps per solve (<= 0: 60) */
+  int reserved2;
 } lyap_opts_t;
 
 /*
@@ -131,7 +133,18 @@ typedef struct {
  * n_inversions count the stored shifted inverses, and mu[j] holds the shift p_j (of the
  * power-of-two prescaled A).
  */
-typedef enum { LYAP_INNER_SIGN = 0, LYAP_INNER_ADI = 1 } lyap_inner_t;
+typedef enum { LYAP_INNER_SIGN = 0, LYAP_INNER_ADI = 1, LYAP_INNER_EKSM = 2 } lyap_inner_t;
+/*
+ * LYAP_INNER_EKSM: the extended Krylov (Galerkin) method, the Krylov alternative Sec. 5
+ * names (no counterpart in the paper's experiments): V spans {L, A^-1 L, A L, A^-2 L, ...}
+ * in orthonormal blocks of 2m columns (A^-1 computed once at u_s and stored, products with
+ * A in the working precision of u_s), the projected equation V^T A V Y + Y V^T A^T V + V^T L S
+ * L^T V = 0 is solved by the FP64 sign-Newton solver on an internal context (V^T A V must be
+ * stable: A + A^T < 0 guarantees it), X = V Y V^T, and the iteration stops when
+ * sqrt(2) ||U_next^T A V Y||_F (its residual norm) is <= adi_tol ||L S L^T||_F, on breakdown
+ * of the next block, or after eksm_maxit blocks.  The stored A^-1 serves every correction
+ * solve and the adjoint.  n_inversions counts the one stored inverse.
+ */
 
 /* Phases reported in lyap_info_t.phase_ms / phase_calls / phase_flops when
  * opts.profile = 1 (LYAP_NUM_PHASES slots; the unused ones stay zero). */

@@ -87,6 +87,7 @@ struct lyap_ctx {
   // stored inverse sequence (Sec. 3.4)
   lyap::Buf store, dmu, dex;
   int store_n = 0, store_prec = -1, store_count = 0, store_e0 = 0;
+  bool store_t = false;  // the stored inverses are transposed (the adjoint's replay)
   double store_fp = 0.0;   // fingerprint of the matrix whose inverse sequence is stored
   size_t store_elt = 0;
   int64_t store_ld = 0;    // row pitch (elements) of a stored inverse
@@ -112,6 +113,9 @@ struct lyap_ctx {
   lyap::Buf pnw; // power-iteration vectors of the 2-norm / spectral-radius scalings
   lyap::Buf adiW, adiY, adiG;  // low-rank ADI: [W, V] (working precision), weights of W, W^T W
   std::vector<double> adi_p;   // low-rank ADI: the shifts of the stored inverses
+  // extended Krylov: basis, A times basis, new block, right-hand side, projected matrices
+  lyap::Buf ekV, ekAV, ekW, ekL, ekT, ekE, ekS, ekZY, ekD, ekH, ekTau, ekP, ekQ, ekR;
+  lyap_ctx* sub = nullptr;     // context of the projected (small) Lyapunov solves
   lyap::Buf eigWork32, eigBig, eigX, eigR, eigS, eigHX, eigE, eigLam, eigRed, eigW, eigPv, eigInt;
   void* hpin = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -807,6 +811,7 @@ static int fingerprint(Ctx& C, const double* A, int n, int64_t lda, double* out)
 // Transpose every stored inverse in place: A_k^{-1} -> A_k^{-T} (and back).
 static int transpose_store(Ctx& C) {
   if (C.store_count == 0) return LYAP_OK;
+  C.store_t = !C.store_t;
   const int n = C.store_n;
   const unsigned nt = (unsigned)ceil_div(n, 32);
   // checkpoint mode: the iterates are transposed (A_k -> A_k^T); the inverses recomputed
@@ -1114,6 +1119,262 @@ static int adi_run(Ctx& C, int n, int m, bool ldlt, const NewtonOpts& o, const A
   return LYAP_OK;
 }
 
+static int solve_entry(lyap_ctx_t* C, const double* A, int64_t n, int64_t lda, const double* L, int64_t ldl,
+                       int64_t m, const double* S, int64_t lds, const lyap_opts_t* opts, double* Z, int64_t ldz,
+                       int64_t z_cap, double* D, int64_t* rank_out, lyap_info_t* info, bool refine);
+
+// diag(R) of the leading q columns of a Householder-factored F (ld): out[j] = |F[j, j]|
+template <typename T>
+__global__ void ek_rdiag_kernel(const T* __restrict__ F, int64_t ld, int q, double* __restrict__ out) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < q; j += gridDim.x * blockDim.x)
+    out[j] = fabs((double)F[j + (int64_t)j * ld]);
+}
+
+// Extended Krylov (Galerkin) on Z (working precision; the right-hand side factor L in C.Zw,
+// n x m, weights in C.yv for LDL^T).  compute == true: A0^{-1} (A0 = the prescaled working
+// matrix) is inverted at u_s and stored in slot 0, as the Newton sequence; else reused.  The
+// basis V = [U_1, U_2, ...] (orthonormal blocks of 2m columns): U_1 = orth([L, A0^{-1} L]),
+// U_{j+1} = orth([A0 U_j^(1), A0^{-1} U_j^(2)] minus its projection on V, twice).  With
+// T = V^T A0 V and E = V^T L the projected equation T Y + Y T^T + E S E^T = 0 is solved by
+// the FP64 sign-Newton solver on a context of its own (T must be stable: A0 + A0^T < 0
+// guarantees it); the residual norm is sqrt(2) ||U_{j+1}^T A0 V Y||_F, and the iteration
+// stops once it is <= tol ||L S L^T||_F (or on breakdown of the new block, or at maxit).
+// Result Z = V Z_Y (weights D_Y) in C.Zw / C.yv, *c_out its columns.
+template <typename T>
+static int eksm_run(Ctx& C, int n, int m, bool ldlt, const NewtonOpts& o, int maxit, double tol, bool compute,
+                    int* c_out) {
+  NewtonState* st = P<NewtonState>(C.state);
+  T* Z = P<T>(C.Zw);
+  double* y = P<double>(C.yv);
+  const bool s16 = is16(o.prec);
+  T* A0 = P<T>(C.A0);
+  if (compute) {
+    mark(C, LYAP_PHASE_INVERT);
+    LYAP_TRY(invert_current<T>(C, A0, n, o.prec));
+    mark(C, LYAP_PHASE_NEWTON);
+    const T* X = (const T*)C.gj.M[C.gj.cur];
+    pinv_kernel<<<nblk(n), 256, 0, C.s>>>(C.gj.perm[C.gj.cur], P<int>(C.pinv), n);
+    LYAP_TRY(maxabs<T>(X, n, n, n, &st->maxX, P<double>(C.part), C.s));
+    adi_exp_kernel<<<1, 1, 0, C.s>>>(&st->maxX, 0, s16 ? 1 : 0, P<int>(C.dex), P<double>(C.dmu));
+    void* slot = inv_slot(C, 0);
+    const unsigned nb = (unsigned)std::min<int64_t>(4096, ceil_div((int64_t)n * n, 256));
+    switch (o.prec) {
+      case LYAP_FP64:
+        adi_store_kernel<double, double><<<nb, 256, 0, C.s>>>(n, (const double*)X, P<int>(C.pinv), P<int>(C.dex), 0,
+                                                            (double*)slot, C.store_ld);
+        break;
+      case LYAP_FP32:
+        adi_store_kernel<float, float><<<nb, 256, 0, C.s>>>(n, (const float*)X, P<int>(C.pinv), P<int>(C.dex), 0,
+                                                          (float*)slot, C.store_ld);
+        break;
+      case LYAP_FP16:
+        adi_store_kernel<float, __half><<<nb, 256, 0, C.s>>>(n, (const float*)X, P<int>(C.pinv), P<int>(C.dex), 0,
+                                                           (__half*)slot, C.store_ld);
+        break;
+      case LYAP_BF16:
+        adi_store_kernel<float, __nv_bfloat16><<<nb, 256, 0, C.s>>>(n, (const float*)X, P<int>(C.pinv),
+                                                                  P<int>(C.dex), 0, (__nv_bfloat16*)slot,
+                                                                  C.store_ld);
+        break;
+    }
+    LYAP_CUDA_TRY(cudaGetLastError());
+    lyap_count_launch(3);
+    int gjs = 0;
+    LYAP_TRY(sync_read(C, C.gj.status, &gjs, sizeof(int)));
+    if (gjs) return gjs;
+    C.store_count = 1;
+  } else if (C.store_count != 1) {
+    lyap_set_error_message("no stored inverse for the extended Krylov solver", __FILE__, __LINE__);
+    return LYAP_ERR_ARG;
+  }
+  if (!C.sub) LYAP_TRY(lyap_ctx_create(&C.sub, C.s));
+  LYAP_TRY(lyap_ctx_set_stream(C.sub, C.s));
+  const int b = 2 * m;                                    // block width
+  const int kcap = std::min(n, b * (maxit + 1));
+  const size_t te = sizeof(T);
+  LYAP_TRY(ensure(C.ekV, (size_t)n * (kcap + b) * te + 64));
+  LYAP_TRY(ensure(C.ekAV, (size_t)n * (kcap + b) * te + 64));
+  LYAP_TRY(ensure(C.ekW, (size_t)n * 2 * b * te + 64));
+  LYAP_TRY(ensure(C.ekL, (size_t)n * m * te + 64));
+  LYAP_TRY(ensure(C.ekT, (size_t)kcap * kcap * 8 + 64));
+  LYAP_TRY(ensure(C.ekE, (size_t)kcap * m * 8 + 64));
+  LYAP_TRY(ensure(C.ekS, (size_t)m * m * 8 + 64));
+  LYAP_TRY(ensure(C.ekZY, (size_t)kcap * kcap * 8 + 64));
+  LYAP_TRY(ensure(C.ekD, (size_t)kcap * 8 + 64));
+  LYAP_TRY(ensure(C.ekH, (size_t)(kcap + b) * b * te + 64));
+  LYAP_TRY(ensure(C.ekTau, (size_t)(b + 8) * te));
+  LYAP_TRY(ensure(C.ekP, (size_t)b * kcap * 8 + 64));
+  LYAP_TRY(ensure(C.ekQ, (size_t)std::max<int64_t>((int64_t)kcap * kcap, (int64_t)b * kcap) * 8 + 64));
+  LYAP_TRY(ensure(C.ekR, (size_t)(b + 8) * 8));
+  LYAP_TRY(ensure(C.qrWork, (size_t)n * b * te + 64));
+  T* V = P<T>(C.ekV);
+  T* AV = P<T>(C.ekAV);
+  T* W = P<T>(C.ekW);       // [W | scratch] n x 2b
+  T* Lr = P<T>(C.ekL);
+  T* H = P<T>(C.ekH);
+  T* tauq = P<T>(C.ekTau);
+  double* sc = P<double>(C.scal) + 56;
+  LYAP_CUDA_TRY(cudaMemcpyAsync(Lr, Z, te * (size_t)n * m, cudaMemcpyDeviceToDevice, C.s));
+  // weights of the right-hand side (S = diag(y0)) as an m x m FP64 matrix for the small solves
+  std::vector<double> y0(m, 1.0);
+  if (ldlt) LYAP_TRY(sync_read(C, y, y0.data(), sizeof(double) * m));
+  {
+    std::vector<double> Sh((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i) Sh[(size_t)i * m + i] = y0[i];
+    LYAP_CUDA_TRY(cudaMemcpyAsync(C.ekS.p, Sh.data(), sizeof(double) * m * m, cudaMemcpyHostToDevice, C.s));
+    LYAP_CUDA_TRY(cudaStreamSynchronize(C.s));
+  }
+  // ||L S L^T||_F^2 through the Gram matrix of L
+  double nrm0 = 0.0;
+  {
+    LYAP_TRY(ensure(C.Lst, (size_t)n * m * 8 + 64));
+    double* L64 = P<double>(C.Lst);
+    LYAP_TRY((copy_cast<T, double>(Lr, n, m, n, L64, n, 1.0, C.s)));
+    LYAP_TRY(gemm<double>('T', 'N', m, m, n, 1.0, L64, n, L64, n, 0.0, P<double>(C.ekP), m, C.s));
+    adi_resnorm_kernel<<<1, 256, 0, C.s>>>(P<double>(C.ekP), m, ldlt ? y : nullptr, sc);
+    LYAP_CUDA_TRY(cudaGetLastError());
+    lyap_count_launch();
+    LYAP_TRY(sync_read(C, sc, &nrm0, sizeof(double)));
+    nrm0 = std::sqrt(nrm0);
+  }
+  if (!(nrm0 > 0.0)) {
+    *c_out = 0;
+    return LYAP_OK;
+  }
+  mark(C, LYAP_PHASE_FACTOR);
+  double ek_last_min = 0.0, ek_last_rms = 0.0;
+  // orthonormalise the n x b block Wb (in W) against V[:, :k] (twice) and into V[:, k:k+b];
+  // false on breakdown (a column of the new block below 1e-10 of its size before projection)
+  auto next_block = [&](int k, bool* broke) -> int {
+    double pre = 0.0;
+    LYAP_TRY(sumsq<T>(W, n, b, n, sc, P<double>(C.part), C.s));
+    LYAP_TRY(sync_read(C, sc, &pre, sizeof(double)));
+    for (int pass = 0; pass < 2 && k > 0; ++pass) {
+      LYAP_TRY(gemm<T>('T', 'N', k, b, n, T(1), V, n, W, n, T(0), H, k, C.s));
+      LYAP_TRY(gemm<T>('N', 'N', n, b, k, T(-1), V, n, H, k, T(1), W, n, C.s));
+    }
+    T* F = (T*)C.qrWork.p;
+    LYAP_TRY((copy_cast<T, T>(W, n, b, n, F, n, 1.0, C.s)));
+    LYAP_CUDA_TRY(cudaMemsetAsync(C.qr.status, 0, sizeof(int), C.s));
+    LYAP_TRY(householder_qr<T>(F, n, b, n, tauq, C.qr, C.s));
+    ek_rdiag_kernel<T><<<1, 128, 0, C.s>>>(F, n, b, P<double>(C.ekR));
+    LYAP_CUDA_TRY(cudaGetLastError());
+    lyap_count_launch();
+    std::vector<double> rd(b);
+    LYAP_TRY(sync_read(C, C.ekR.p, rd.data(), sizeof(double) * b));
+    int qs = 0;
+    LYAP_TRY(sync_read(C, C.qr.status, &qs, sizeof(int)));
+    if (qs) return qs;
+    double mn = rd[0];
+    for (double v : rd) mn = std::min(mn, v);
+    ek_last_min = mn;
+    ek_last_rms = std::sqrt(pre / b);
+    *broke = !(mn > 1e-10 * std::sqrt(pre / b));
+    if (*broke) return LYAP_OK;
+    // explicit Q: V[:, k:k+b] = Q [I; 0]
+    LYAP_TRY(set_identity<T>(H, b, b, C.s));
+    LYAP_TRY(apply_q<T>(F, n, b, n, tauq, H, b, b, V + (size_t)k * n, n, C.s));
+    // A0 times the new block (A0 is row-major: the transpose of a column-major matrix; while
+    // the store is transposed for the adjoint, the operator is A0^T)
+    LYAP_TRY(gemm<T>(C.store_t ? 'N' : 'T', 'N', n, b, n, T(1), A0, n, V + (size_t)k * n, n, T(0),
+                     AV + (size_t)k * n, n, C.s));
+    return LYAP_OK;
+  };
+  // U_1 = orth([L, A0^{-1} L]); when it has n columns or more the space is all of R^n and the
+  // projected equation is the equation itself (V = I)
+  const bool full = (b >= n);
+  bool broke = false;
+  if (full) {
+    LYAP_TRY(set_identity<T>(V, n, n, C.s));
+    LYAP_TRY(gemm<T>(C.store_t ? 'N' : 'T', 'N', n, n, n, T(1), A0, n, V, n, T(0), AV, n, C.s));
+  } else {
+    LYAP_CUDA_TRY(cudaMemcpyAsync(W, Lr, te * (size_t)n * m, cudaMemcpyDeviceToDevice, C.s));
+    LYAP_TRY(factor_product<T>(C, n, m, o.prec, 0, W));   // W[:, m:2m] = A0^{-1} L
+    LYAP_TRY(next_block(0, &broke));
+    if (broke) {
+      char msg[160];
+      snprintf(msg, sizeof(msg), "extended Krylov: the first block [L, A^-1 L] is rank deficient (n %d, m %d, "
+               "min |r_jj| %.3e, rms column %.3e)", n, m, ek_last_min, ek_last_rms);
+      lyap_set_error_message(msg, __FILE__, __LINE__);
+      return LYAP_ERR_NOCONV;
+    }
+  }
+  int k = full ? n : b;  // columns of V in the current projection
+  int kY = k;            // columns of V that Z_Y belongs to
+  int rY = 0;            // columns of Z_Y
+  lyap_opts_t so;
+  lyap_opts_default(&so);
+  so.u_s = LYAP_FP64;
+  so.rho = 0.0;
+  for (int it = 0; it < maxit; ++it) {
+    broke = full;
+    if (!full) {
+      // the next block from U_j = V[:, k-b:k]: [A0 U^(1), A0^{-1} U^(2)]
+      LYAP_CUDA_TRY(cudaMemcpyAsync(W, AV + (size_t)(k - b) * n, te * (size_t)n * m, cudaMemcpyDeviceToDevice, C.s));
+      T* Ws = W + (size_t)b * n;  // scratch [U^(2) | A0^{-1} U^(2)]
+      LYAP_CUDA_TRY(cudaMemcpyAsync(Ws, V + (size_t)(k - m) * n, te * (size_t)n * m, cudaMemcpyDeviceToDevice, C.s));
+      LYAP_TRY(factor_product<T>(C, n, m, o.prec, 0, Ws));
+      LYAP_CUDA_TRY(cudaMemcpyAsync(W + (size_t)m * n, Ws + (size_t)m * n, te * (size_t)n * m,
+                                    cudaMemcpyDeviceToDevice, C.s));
+      const bool room = (k + b <= n) && (k + b <= kcap);
+      broke = !room;
+      if (room) LYAP_TRY(next_block(k, &broke));
+    }
+    // projected equation on V[:, :k]: T = V^T A0 V, E = V^T L (FP64)
+    {
+      T* Tw = (T*)C.ekQ.p;  // k x k
+      LYAP_TRY(gemm<T>('T', 'N', k, k, n, T(1), V, n, AV, n, T(0), Tw, k, C.s));
+      LYAP_TRY((copy_cast<T, double>(Tw, k, k, k, P<double>(C.ekT), k, 1.0, C.s)));
+      LYAP_TRY(gemm<T>('T', 'N', k, m, n, T(1), V, n, Lr, n, T(0), Tw, k, C.s));
+      LYAP_TRY((copy_cast<T, double>(Tw, k, m, k, P<double>(C.ekE), k, 1.0, C.s)));
+    }
+    int64_t r64 = 0;
+    lyap_info_t sinfo;
+    LYAP_TRY(solve_entry(C.sub, P<double>(C.ekT), k, k, P<double>(C.ekE), k, m, ldlt ? P<double>(C.ekS) : nullptr, m,
+                         &so, P<double>(C.ekZY), k, k, ldlt ? P<double>(C.ekD) : nullptr, &r64, &sinfo, false));
+    rY = (int)r64;
+    kY = k;
+    if (broke) break;  // invariant subspace, all of R^n, or no room: the projection on V is the answer
+    // residual: sqrt(2) ||U_{j+1}^T A0 V Y||_F with Y = Z_Y D Z_Y^T
+    {
+      T* Tw = (T*)C.ekQ.p;
+      LYAP_TRY(gemm<T>('T', 'N', b, k, n, T(1), V + (size_t)k * n, n, AV, n, T(0), Tw, b, C.s));  // tau (b x k)
+      double* tau64 = P<double>(C.ekP);
+      LYAP_TRY((copy_cast<T, double>(Tw, b, k, b, tau64, b, 1.0, C.s)));
+      double* PZ = P<double>(C.ekQ);
+      LYAP_TRY(gemm<double>('N', 'N', b, rY, k, 1.0, tau64, b, P<double>(C.ekZY), k, 0.0, PZ, b, C.s));
+      if (ldlt) LYAP_TRY(scale_cols<double>(PZ, b, rY, b, P<double>(C.ekD), C.s));
+      double* PY = P<double>(C.ekP);
+      LYAP_TRY(gemm<double>('N', 'T', b, k, rY, 1.0, PZ, b, P<double>(C.ekZY), k, 0.0, PY, b, C.s));
+      LYAP_TRY(sumsq<double>(PY, b, k, b, sc, P<double>(C.part), C.s));
+      double r2 = 0.0;
+      LYAP_TRY(sync_read(C, sc, &r2, sizeof(double)));
+      if (!std::isfinite(r2)) return LYAP_ERR_NONFINITE;
+      if (std::sqrt(2.0 * r2) <= tol * nrm0) break;
+    }
+    k += b;
+  }
+  // Z = V[:, :k] Z_Y (working precision), weights D_Y
+  if (rY > 2 * n + 8) {
+    lyap_set_error_message("extended Krylov factor exceeds its capacity", __FILE__, __LINE__);
+    return LYAP_ERR_CAPACITY;
+  }
+  {
+    T* ZYw = (T*)C.ekQ.p;
+    LYAP_TRY((copy_cast<double, T>(P<double>(C.ekZY), kY, rY, kY, ZYw, kY, 1.0, C.s)));
+    LYAP_TRY(gemm<T>('N', 'N', n, rY, kY, T(1), V, n, ZYw, kY, T(0), Z, n, C.s));
+    if (ldlt) LYAP_CUDA_TRY(cudaMemcpyAsync(y, C.ekD.p, sizeof(double) * rY, cudaMemcpyDeviceToDevice, C.s));
+  }
+  mark(C, LYAP_PHASE_OTHER);
+  if (s16) {
+    int tcs = 0;
+    LYAP_TRY(tc_status_read(&tcs));
+    if (tcs) return tcs;
+  }
+  *c_out = rY;
+  return LYAP_OK;
+}
+
 // Run the sign-Newton factor iteration on Z (working precision, n x c0 in C.Zw, column-major).
 // compute == true: compute and store the inverse sequence from the working
 // matrix in C.A0 (row-major, already scaled); else replay the stored sequence.
@@ -1371,6 +1632,7 @@ int lyap_opts_default(lyap_opts_t* o) {
   o->inner = LYAP_INNER_SIGN;
   o->adi_shifts = 8;
   o->adi_maxit = 200;
+  o->eksm_maxit = 60;
   return LYAP_OK;
 }
 
@@ -1412,8 +1674,10 @@ int lyap_ctx_destroy(lyap_ctx_t* C) {
                 &C->Lm, &C->Zs, &C->Zbest, &C->G, &C->gram, &C->ysol, &C->ybest, &C->ytmp, &C->Lw, &C->Sd,
                 &C->Vs, &C->Lst, &C->Rtau, &C->Bm, &C->VB, &C->qrBar, &C->qrStatus, &C->qrCand, &C->qrNorms, &C->qrPiv, &C->qrRdiag, &C->qrWork,
                 &C->qrRank, &C->eigWork32, &C->eigBig, &C->eigX, &C->eigR, &C->eigS, &C->eigHX, &C->eigE, &C->eigLam,
-                &C->eigRed, &C->eigW, &C->eigPv, &C->eigInt, &C->At, &C->Ct, &C->ZY, &C->adjT, &C->Hf, &C->tl, &C->inv1, &C->pnw, &C->adiW, &C->adiY, &C->adiG};
+                &C->eigRed, &C->eigW, &C->eigPv, &C->eigInt, &C->At, &C->Ct, &C->ZY, &C->adjT, &C->Hf, &C->tl, &C->inv1, &C->pnw, &C->adiW, &C->adiY, &C->adiG, &C->ekV, &C->ekAV, &C->ekW, &C->ekL,
+                &C->ekT, &C->ekE, &C->ekS, &C->ekZY, &C->ekD, &C->ekH, &C->ekTau, &C->ekP, &C->ekQ, &C->ekR};
   for (Buf* b : all) free_buf(*b);
+  if (C->sub) lyap_ctx_destroy(C->sub);
   for (lyap_ctx* w : C->pool) lyap_ctx_destroy(w);
   for (cudaStream_t st : C->pool_streams) cudaStreamDestroy(st);
   if (C->hpin) cudaFreeHost(C->hpin);
@@ -1572,7 +1836,7 @@ static int newton_solve(Ctx& C, const Problem& pb, const double* Lr, int mr, con
     // sequence of kmax inverses would exceed mem_budget
     int ce = o.ckpt_every > 0 ? o.ckpt_every : 0;
     if (ce == 0 && o.mem_budget > 0 && (double)no.kmax * (double)inv_bytes > (double)o.mem_budget) ce = 4;
-    if (o.inner == LYAP_INNER_ADI) ce = 0;  // the shifted inverses are always stored
+    if (o.inner != LYAP_INNER_SIGN) ce = 0;  // the (shifted) inverses of ADI / EKSM are always stored
     C.store_ckpt = ce;
     C.store_welt = sizeof(T);
     if (ce) {
@@ -1584,6 +1848,7 @@ static int newton_solve(Ctx& C, const Problem& pb, const double* Lr, int mr, con
       if (padded) LYAP_CUDA_TRY(cudaMemsetAsync(C.store.p, 0, (size_t)no.kmax * inv_bytes, C.s));
     }
     C.store_elt = selt;
+    C.store_t = false;
     C.store_n = n;
     C.store_prec = o.u_s;
     C.store_count = 0;
@@ -1625,13 +1890,17 @@ static int newton_solve(Ctx& C, const Problem& pb, const double* Lr, int mr, con
     }
   }
   int c = 0;
-  const bool adi = (o.inner == LYAP_INNER_ADI);
-  if (adi) {
+  // ADI and EKSM iterates approximate X itself (no final factor of the Newton form)
+  const bool adi = (o.inner != LYAP_INNER_SIGN);
+  const double itol = o.adi_tol > 0 ? o.adi_tol : std::max(10.0 * unit_roundoff(o.u_s), 1e-14);
+  if (o.inner == LYAP_INNER_ADI) {
     AdiOpts ao;
     ao.shifts = o.adi_shifts > 0 ? o.adi_shifts : 8;
     ao.maxit = o.adi_maxit > 0 ? o.adi_maxit : 200;
-    ao.tol = o.adi_tol > 0 ? o.adi_tol : std::max(10.0 * unit_roundoff(o.u_s), 1e-14);
+    ao.tol = itol;
     LYAP_TRY(adi_run<T>(C, n, mr, ldlt, no, ao, compute, &c, info));
+  } else if (o.inner == LYAP_INNER_EKSM) {
+    LYAP_TRY(eksm_run<T>(C, n, mr, ldlt, no, o.eksm_maxit > 0 ? o.eksm_maxit : 60, itol, compute, &c));
   } else {
     LYAP_TRY(newton_run<T>(C, n, mr, ldlt, no, compute, &c, info));
   }
@@ -1643,7 +1912,7 @@ static int newton_solve(Ctx& C, const Problem& pb, const double* Lr, int mr, con
   }
   // undo the prescaling: X = 2^-e0 X'  ->  Z = 2^{-e0/2} Z' (Cholesky, with the final 1/sqrt 2),
   // Y = 2^-e0 Y'/2 (LDL^T)
-  // (the ADI factor carries no final 1/sqrt 2 / 1/2: its iterates approximate X itself)
+  // (ADI and EKSM factors carry no final 1/sqrt 2 / 1/2: their iterates approximate X itself)
   const double e0 = (double)C.store_e0;
   if (!ldlt) {
     LYAP_TRY((copy_cast<T, double>(P<T>(C.Zw), n, c, n, Zout, ldo, pow(2.0, -0.5 * e0) / (adi ? 1.0 : sqrt(2.0)),
@@ -1889,7 +2158,7 @@ static int check_problem(const Problem& pb, const lyap_opts_t* o, double* Z, int
   if (pb.n <= 0 || pb.m <= 0 || pb.lda < pb.n || pb.ldl < pb.n || ldz < pb.n || z_cap <= 0) return LYAP_ERR_ARG;
   if (pb.S && pb.lds < pb.m) return LYAP_ERR_ARG;
   if (o->u_s < 0 || o->u_s > 3 || o->scaling < 0 || o->scaling > 4 || o->kmax <= 0 || o->imax < 0) return LYAP_ERR_ARG;
-  if (o->inner != LYAP_INNER_SIGN && o->inner != LYAP_INNER_ADI) return LYAP_ERR_ARG;
+  if (o->inner != LYAP_INNER_SIGN && o->inner != LYAP_INNER_ADI && o->inner != LYAP_INNER_EKSM) return LYAP_ERR_ARG;
   if (o->u != o->u_r || o->u != o->u_c || (o->u != LYAP_FP64 && o->u != LYAP_FP32)) {
     lyap_set_error_message("u = u_r = u_c must be LYAP_FP64 or LYAP_FP32", __FILE__, __LINE__);
     return LYAP_ERR_ARG;

@@ -16,8 +16,8 @@ from . import build_lib
 
 FP64, FP32, FP16, BF16 = 0, 1, 2, 3
 PREC = {"fp64": FP64, "fp32": FP32, "fp16": FP16, "bf16": BF16}
-INNER_SIGN, INNER_ADI = 0, 1
-INNER = {"sign": INNER_SIGN, "adi": INNER_ADI}
+INNER_SIGN, INNER_ADI, INNER_EKSM = 0, 1, 2
+INNER = {"sign": INNER_SIGN, "adi": INNER_ADI, "eksm": INNER_EKSM}
 SCALE_FROB, SCALE_DET, SCALE_NONE, SCALE_NORM2, SCALE_SPECTRAL = 0, 1, 2, 3, 4
 SCALING = {"frob": SCALE_FROB, "det": SCALE_DET, "none": SCALE_NONE, "norm2": SCALE_NORM2,
            "spectral": SCALE_SPECTRAL}
@@ -40,7 +40,7 @@ class LyapOpts(C.Structure):
         ("eta_s", C.c_double), ("stag_theta", C.c_double), ("stag_count", C.c_int), ("project_psd", C.c_int),
         ("profile", C.c_int), ("ckpt_every", C.c_int), ("mem_budget", C.c_int64), ("fp64_products", C.c_int),
         ("u", C.c_int), ("u_r", C.c_int), ("u_c", C.c_int), ("inner", C.c_int), ("adi_shifts", C.c_int),
-        ("adi_maxit", C.c_int), ("adi_tol", C.c_double),
+        ("adi_maxit", C.c_int), ("adi_tol", C.c_double), ("eksm_maxit", C.c_int), ("reserved2", C.c_int),
     ]
 
 

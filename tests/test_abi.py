@@ -37,8 +37,8 @@ def test_struct_layout_matches_header():
     from paper_2510_02126_gb300 import lyap as liblyap
     # u_s, scaling | tau_newton | newton_norm_fro, stop_after, delta_rule (+pad) | scale_off, rank_tol,
     # rho | kmax, imax | tau_ir, eta_r, eta_s, stag_theta | stag_count, project_psd, profile,
-    # ckpt_every | mem_budget | fp64_products, u, u_r, u_c, inner, adi_shifts, adi_maxit (+pad) | adi_tol
-    assert ctypes.sizeof(liblyap.LyapOpts) == 4 * 2 + 8 + 4 * 4 + 8 * 3 + 4 * 2 + 8 * 4 + 4 * 4 + 8 + 4 * 8 + 8
+    # ckpt_every | mem_budget | fp64_products, u, u_r, u_c, inner, adi_shifts, adi_maxit (+pad) | adi_tol | eksm_maxit, reserved2
+    assert ctypes.sizeof(liblyap.LyapOpts) == 4 * 2 + 8 + 4 * 4 + 8 * 3 + 4 * 2 + 8 * 4 + 4 * 4 + 8 + 4 * 8 + 8 + 4 * 2
     assert ctypes.sizeof(liblyap.LyapInfo) == 4 * 10 + 8 + 8 * 64 * 2 + 8 + 8 + 8 * 12 * 3
 
 

@@ -250,3 +250,19 @@ def test_adjoint_with_adi_inner_matches_oracle():
     ref = O.adjoint(A, L, Cm)
     assert relF(N(out["dA"]), ref["dA"]) <= 1e-9
     assert relF(N(out["dL"]), ref["dL"]) <= 1e-9
+
+
+def test_adjoint_with_eksm_inner_matches_oracle():
+    # the adjoint replays the stored A^-1 transposed and applies A^T in the Krylov products
+    lp = lib()
+    d = gen.paper_synthetic(64, 1.0)
+    A, L = d["A"], d["L"]
+    Cm = gen.rng(gen.SEED_BASE + 53).standard_normal((3, 64))
+    o = lp.make_opts(u_s="fp16", inner="eksm", tau_ir=1e-13, imax=30)
+    Z, _, info = lp.solve_ir(T(A), T(L), opts=o)
+    assert info.converged
+    out = lp.adjoint(T(A), T(L), Z, T(Cm), opts=o)
+    assert out["info"].converged
+    ref = O.adjoint(A, L, Cm)
+    assert relF(N(out["dA"]), ref["dA"]) <= 1e-9
+    assert relF(N(out["dL"]), ref["dL"]) <= 1e-9

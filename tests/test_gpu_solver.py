@@ -424,3 +424,38 @@ def test_ir_ldlt_adi_inner_indefinite():
     assert info.converged, info.as_dict()
     assert rel((N(Z) * N(D)) @ N(Z).T, X) <= 1e-10
     assert O.residual_eq41(A, N(Z), W, N(D)) <= 1e-12
+
+
+# ------------------------------------------------ extended Krylov as the inner solver
+
+def test_eksm_single_solve_fp64_matches_bartels_stewart():
+    # lyap_sign_solve with inner = EKSM at FP64 (Sec. 4.2 family: symmetric negative definite A,
+    # so every projected matrix is stable): one Galerkin solve to a residual of 1e-14
+    d = gen.paper_synthetic(100, 1.0)
+    A, L = d["A"], d["L"]
+    X = O.bartels_stewart(A, L @ L.T)
+    Z, _, info = lib().sign_solve(T(A), T(L), u_s="fp64", inner="eksm")
+    assert rel(N(Z) @ N(Z).T, X) <= 1e-10
+    assert info.n_inversions == 1
+
+
+@pytest.mark.parametrize("form", ["chol", "ldlt"])
+def test_ir_eksm_inner_matches_bartels_stewart(form):
+    # the refinement with extended Krylov inner solves (A^-1 stored once at FP16 and reused by
+    # every correction) reaches 1e-12 and the exact solution, as the oracle's does
+    d = gen.paper_synthetic(200, 1.5)
+    A, L = d["A"], d["L"]
+    S = np.diag([1.0, -1.0, 1.0]) if form == "ldlt" else np.eye(3)
+    W = L @ S @ L.T
+    X = O.bartels_stewart(A, W)
+    Z, D, info = lib().solve_ir(T(A), T(L), S=T(S) if form == "ldlt" else None, u_s="fp16", inner="eksm",
+                                tau_ir=1e-12, imax=30)
+    assert info.converged, info.as_dict()
+    Xg = (N(Z) * N(D)) @ N(Z).T if form == "ldlt" else N(Z) @ N(Z).T
+    assert rel(Xg, X) <= 1e-10
+    assert info.n_inversions == 1
+    if form == "chol":
+        _, io = O.ir_chol(A, L, O.Opts(u_s="fp16", inner="eksm", tau_ir=1e-12, imax=30))
+    else:
+        _, _, io = O.ir_ldlt(A, L, S, O.Opts(u_s="fp16", inner="eksm", tau_ir=1e-12, imax=30))
+    assert io.converged
