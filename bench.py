@@ -441,6 +441,9 @@ def run_case(args):
                         Newton steps) + lyap_adjoint of l = trace(C X C^T) (p = 2 family, m = 4,
                         C 4 x n): times, and central differences of FP64 sign-Newton losses on k
                         (default 20) random directions of A and L (relative errors)
+    inner[:<n>[:<q>[:<u>]]]  the sign-Newton, low-rank ADI and extended Krylov inner solvers of the
+                        refinement on the Sec. 4.2 family (default n = 1000, q = 1, u = fp16) and
+                        the FP64 sign-Newton solver: ms per solve, steps, inversions, rank
     kappa_sign          kappa_sign(B) of B = [[A, W], [0, -A^T]] (lyap_kappa_sign) for the n = 1024
                         workload and the block-normal family at n = 1024, p = 1..4
     config1             FP64 sign-Newton on the 8 x 8-grid Laplacian (n = 64, determinantal scaling,
@@ -676,6 +679,41 @@ def run_case(args):
                           "fd_precision": "fp64 sign-Newton losses",
                           "max_rel_err_dA": mx(rel_A), "max_rel_err_dL": mx(rel_L),
                           "max_err_dA_over_grad_norm": mx(nrm_A), "max_err_dL_over_grad_norm": mx(nrm_L)}))
+        return 0
+    elif kind == "inner":
+        # the three inner solvers of the refinement on the Sec. 4.2 family (symmetric A, real
+        # spectrum): sign-Newton, low-rank ADI, extended Krylov; FP16 inner solves (or u),
+        # FP64 refinement to 1e-12; and the FP64 sign-Newton solver (CUDA events, 2 timed runs
+        # after one warm-up)
+        import lyapgen
+        n = int(rest[0]) if rest else 1000
+        q = float(rest[1]) if len(rest) > 1 else 1.0
+        u = rest[2] if len(rest) > 2 else "fp16"
+        d = lyapgen.paper_synthetic(n, q)
+        A, L = torch.tensor(d["A"], device=dev), torch.tensor(d["L"], device=dev)
+        stream = torch.cuda.current_stream()
+        runs = [("ir", inner, lyap.make_opts(u_s=u, inner=inner, tau_ir=TAU, imax=30))
+                for inner in ("sign", "adi", "eksm")]
+        runs.append(("sign_newton", "sign", lyap.make_opts(u_s="fp64")))
+        for solver, inner, o in runs:
+            fn = lyap.solve_ir if solver == "ir" else lyap.sign_solve
+            try:
+                fn(A, L, opts=o)
+                ms = []
+                for _ in range(2):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    Z, _, info = fn(A, L, opts=o)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                print(json.dumps({"case": "inner", "n": n, "q": q, "solver": solver, "inner": inner,
+                                  "u_s": "fp64" if solver == "sign_newton" else u, "ms_per_solve": min(ms),
+                                  "res_final": info.res_final, "converged": bool(info.converged or solver != "ir"),
+                                  "ir_steps": info.ir_steps, "inversions": info.n_inversions, "rank": info.rank}),
+                      flush=True)
+            except lyap.LyapError as e:
+                print(json.dumps({"case": "inner", "n": n, "q": q, "inner": inner, "error": str(e)}), flush=True)
         return 0
     elif kind == "kappa_sign":
         # kappa_sign(B), B = [[A, W], [0, -A^T]] (Sec. 4.2), for the n = 1024 convection-
