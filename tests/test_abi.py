@@ -46,6 +46,21 @@ def test_opts_default_without_gpu():
     from paper_2510_02126_gb300 import lyap as liblyap
     o = liblyap.make_opts()
     assert o.rho == 0.1 and o.imax == 50 and o.kmax == 50 and o.eta_r == 1e-4 and o.stop_after == 2
+    # the options beyond the paper's: sign-Newton inner solver, FP64 working precision
+    assert o.inner == liblyap.INNER_SIGN and o.adi_shifts == 8 and o.adi_maxit == 200 and o.eksm_maxit == 60
+    assert o.u == o.u_r == o.u_c == liblyap.FP64 and o.scaling == liblyap.SCALE_FROB
+
+
+def test_opts_names_map_to_enum_values():
+    from paper_2510_02126_gb300 import lyap as liblyap
+    o = liblyap.make_opts("bf16", inner="eksm", scaling="spectral", adi_tol=1e-9)
+    assert (o.u_s, o.inner, o.scaling, o.adi_tol) == (liblyap.BF16, 2, 4, 1e-9)
+    o = liblyap.make_opts("fp32", inner="adi", scaling="norm2")
+    assert (o.u_s, o.inner, o.scaling) == (liblyap.FP32, 1, 3)
+    header = open(os.path.join(ROOT, "include", "liblyap.h")).read()
+    for name, value in (("LYAP_INNER_ADI", 1), ("LYAP_INNER_EKSM", 2), ("LYAP_SCALE_NORM2", 3),
+                        ("LYAP_SCALE_SPECTRAL", 4)):
+        assert re.search(rf"\b{name} = {value}\b", header), name
 
 
 def test_field_offsets_match_c_compiler(tmp_path):
